@@ -1,0 +1,333 @@
+"""Benchmark of the consensus-ADMM calibration hot path on GB300.
+
+One step = one full calibration of the LOFAR-shaped batch (62 stations / 1891 baselines,
+5 directions of 20-source clusters, 32 subbands 115-185 MHz, 10 solution intervals of 10
+samples, Bernstein degree 3, rho 10, SNR 10): coherency prediction from the sky model,
+a cold start (J = I, Z = Y = 0) and 30 C-ADMM iterations with 10 LM x 4 PCG inner steps.
+Metric: visibilities x directions x ADMM iterations per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank calibrates its own batch (seed offset by rank): no data-path
+collective, weak scaling. --impl reference times the FP64 CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")  # the CPU oracle legs run on one core
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "lofar_n62_k5"
+N_LM, N_CG = 10, 4
+METRIC = "ADMM vis*dir*iter/s (LOFAR-shaped: N=62, K=5, 32 subbands, 10 intervals x 10 samples)"
+UNIT = "vis*dir*iter/s"
+
+# DRAM traffic per launch of the dominant sweep kernel from one ncu capture; valid only for the
+# kernel source it was taken on (sha256 prefix of sweep.cu), else reported as null.
+NCU_TRAFFIC = {}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mp = json.load(fh)
+        return float(mp["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def sweep_hash() -> str:
+    with open(os.path.join(ROOT, "paper_1502_00858_gb300", "csrc", "sweep.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:12]
+
+
+class ClockSampler:
+    """nvidia-smi SM clocks and throttle reasons sampled during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        if not self.rows:
+            return None
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def units(prob) -> float:
+    """Unflagged visibilities x directions per ADMM iteration."""
+    keep = (prob["flags"] == 0).sum(axis=1)
+    return float(np.sum(keep * prob["T"])) * prob["K"]
+
+
+# ----------------------------------------------------------------------------- CPU oracle legs
+
+def oracle_sample(prob, n_freq: int):
+    """One C-ADMM iteration of the FP64 oracle on interval 0 restricted to its first n_freq
+    subbands (same per-agent data, same LM/PCG schedule). Returns (seconds, vis*dir*iter)."""
+    from oracle import admm as O
+
+    sub = dict(prob, P=n_freq, I=1, A=n_freq, basis=prob["basis"][:n_freq], freqs=prob["freqs"][:n_freq],
+               V=prob["V"][:n_freq], C=prob["C"][:n_freq], flags=prob["flags"][:n_freq], T=prob["T"][:n_freq])
+    t0 = time.perf_counter()
+    O.admm(sub, 1, n_lm=N_LM, n_cg=N_CG)
+    dt = time.perf_counter() - t0
+    return dt, units(sub)
+
+
+def cpu_threads() -> int:
+    return 1  # NumPy einsum/matmul on 2x2 blocks runs single-threaded; BLAS pinned to one thread below
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    from synth import make_problem
+
+    prob = make_problem(WORKLOAD, I=1)
+    n_freq = 4
+    for _ in range(args.warmup):
+        oracle_sample(prob, n_freq)
+    tot_t, tot_u = 0.0, 0.0
+    for _ in range(args.steps):
+        dt, u = oracle_sample(prob, n_freq)
+        tot_t += dt
+        tot_u += u
+    value = tot_u / tot_t
+    sample = f"one C-ADMM iteration (10 LM x 4 PCG) of interval 0, first {n_freq} of 32 subbands, per step"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_lm": N_LM, "n_cg": N_CG, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU leg
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_1502_00858_gb300 import Calibrator, capi
+    from synth import make_problem, user_layout
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    capi.load()
+
+    t_gen = time.perf_counter()
+    prob = make_problem(WORKLOAD, seed=1 + rank)
+    ul = user_layout(prob)
+    t_gen = time.perf_counter() - t_gen
+    n_admm = prob["n_admm"]
+    per_iter_units = units(prob)
+
+    stream = torch.cuda.Stream()
+    cal = Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
+                     n_intervals=prob["I"], samples=prob["T"], n_lm=N_LM, n_cg=N_CG,
+                     chunk_diagonals=args.chunk_diagonals, cuda_stream=stream.cuda_stream)
+    dev = torch.device("cuda", local)
+    vis_d = torch.from_numpy(ul["vis"].view(np.float32)).to(dev)
+    uvw_d = torch.from_numpy(np.ascontiguousarray(prob["uvw"])).to(dev)
+    sky_d = torch.from_numpy(np.ascontiguousarray(prob["sky"])).to(dev)
+    J_d = torch.empty(int(np.prod(cal.jones_shape)) * 2, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    capi.calib_set_data(cal.ctx, vis_d)  # device pointers: stream-ordered
+
+    def step():
+        capi.calib_predict(cal.ctx, uvw_d, sky_d, prob["f0"])
+        capi.calib_reset(cal.ctx)
+        capi.calib_admm_iter(cal.ctx, n_admm, want_hist=False)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches0 = capi.calib_launch_count(cal.ctx)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    dt = ev0.elapsed_time(ev1) / 1e3
+    launches = capi.calib_launch_count(cal.ctx) - launches0
+    if world > 1:
+        t = torch.tensor([dt], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        dt = float(t.item())
+    value = world * per_iter_units * n_admm * args.steps / dt
+
+    # per-kernel durations (CUDA events recorded on the library stream around every sweep launch)
+    capi.calib_profile_enable(cal.ctx, True)
+    for _ in range(args.steps):
+        step()
+    prof = capi.calib_profile_read(cal.ctx)
+    capi.calib_profile_enable(cal.ctx, False)
+    dom = max(prof, key=lambda k: prof[k]["total_ms"])
+    avg_s = prof[dom]["total_ms"] / 1e3 / max(1, prof[dom]["launches"])
+    achieved = prof[dom]["bytes_per_launch"] / avg_s / 1e9
+    peak, peak_kind = peaks()
+    h = sweep_hash()
+    traffic = NCU_TRAFFIC.get((dom, h))
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": dom, "peak_source": peak_kind,
+                "per_kernel": {k: {"avg_us": 1e3 * v["total_ms"] / max(1, v["launches"]),
+                                   "launches": v["launches"],
+                                   "GBps": v["bytes_per_launch"] / (v["total_ms"] / 1e3 / max(1, v["launches"])) / 1e9
+                                   if v["launches"] else None,
+                                   "share_of_step": v["total_ms"] / 1e3 / (dt * 1.0) if dt else None}
+                               for k, v in prof.items()}}
+
+    # end to end through the public API with host buffers: H2D of the visibilities, uvw and sky,
+    # prediction, cold start, 30 iterations, D2H of the solutions.
+    vis_h = torch.from_numpy(ul["vis"].view(np.float32)).pin_memory()
+    uvw_h = torch.from_numpy(np.ascontiguousarray(prob["uvw"])).pin_memory()
+    sky_h = torch.from_numpy(np.ascontiguousarray(prob["sky"])).pin_memory()
+    J_h = torch.empty(int(np.prod(cal.jones_shape)) * 2, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        capi.calib_set_data(cal.ctx, vis_h)
+        capi.calib_predict(cal.ctx, uvw_h, sky_h, prob["f0"])
+        capi.calib_reset(cal.ctx)
+        capi.calib_admm_iter(cal.ctx, n_admm, want_hist=False)
+        capi.calib_get_solutions(cal.ctx, J=J_h)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_dt = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_dt], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_dt = float(t.item())
+    e2e_value = world * per_iter_units * n_admm * args.steps / e2e_dt
+    h2d = vis_h.numel() * 4 + uvw_h.numel() * 8 + sky_h.numel() * 8
+    d2h = J_h.numel() * 4
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        n_freq = 8
+        cdt, cu = oracle_sample(prob, n_freq)
+        cpu = {"value": cu / cdt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"one C-ADMM iteration (10 LM x 4 PCG) of interval 0, first {n_freq} of 32 subbands "
+                         f"({cdt:.1f} s)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "stations": prob["N"], "baselines": prob["B"], "directions": prob["K"],
+                       "subbands": prob["P"], "intervals": prob["I"], "samples": 10, "admm_iters": n_admm,
+                       "n_lm": N_LM, "n_cg": N_CG, "basis": "Bernstein degree 3", "rho": 10.0,
+                       "step": "predict + cold start + 30 C-ADMM iterations",
+                       "l2": "inputs larger than L2 (436 MB per residual sweep, 242 MB per Hessian sweep)",
+                       "parallelism": f"replica x{world}" if world > 1 else "single GPU",
+                       "generate_s": round(t_gen, 2)},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(out), flush=True)
+    cal.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--chunk-diagonals", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+        run_reference(args, world, rank)
+        return
+    run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,182 @@
+/*
+ * calib.h - C ABI of the GB300 consensus-ADMM calibration library (libcalib.so).
+ *
+ * The library runs distributed (consensus) radio-interferometric calibration across
+ * frequency, Yatawatta 2015 (arXiv:1502.00858), on one GPU. The paper's P compute
+ * agents - one per frequency f_i - become slices of single kernel launches; several
+ * independent solution intervals (the paper calibrates every 200 s of data
+ * separately, Section 4) are batched the same way. One call of calib_admm_iter runs
+ * C-ADMM iterations (Section 3, Eq. M1-M3, steps D1-D3):
+ *
+ *   M1  J_i <- argmin_J L_i(J, Z, Y_i)       per agent, by Levenberg-Marquardt with a
+ *                                            preconditioned CG step (the paper uses RTR)
+ *   M2  Z   <- closed form of Eq. Zest        per interval and direction (fusion centre)
+ *   M3  Y_i <- Y_i + rho (J_i - B_i Z)        per agent
+ *
+ * with L_i(J,Z,Y) = g(J) + Re tr(Y^H (J - B Z)) + rho/2 ||J - B Z||^2 (Eq. sumtrace2),
+ * g(J) = sum_t sum_{p<q} ||V_pq - sum_k J_pk C_pqk J_qk^H||^2 (Eq. mltheta / Eq. sum3)
+ * and C_pqk = c_pqk I_2 for unpolarised sources (Eq. coh).
+ *
+ * Symbols: N stations, B baselines (pairs p<q), K directions, P frequencies (agents
+ * per interval), M basis terms (the paper calls this F), I solution intervals,
+ * A = I*P agents (agent a = interval*P + frequency index), T_a samples of agent a.
+ *
+ * Conventions for every entry point:
+ *  - Return value: CALIB_OK (0) or a negative CALIB_E* code; calib_last_error() then
+ *    holds a message for the calling thread. No C++ exception or abort crosses the ABI.
+ *  - Complex arrays are interleaved (re, im) float32 ("c64") unless stated as c128.
+ *  - ptr_kind 0: host pointers. The call copies inputs before returning and writes
+ *    outputs before returning (it synchronises the library stream).
+ *    ptr_kind 1: device pointers, ordered on the library stream (calib_options.cuda_stream).
+ *    Device inputs must stay valid until the stream reaches the call; device outputs are
+ *    complete once the stream passes the call (calib_sync waits for it).
+ *  - The context owns all of its device memory and frees it in calib_destroy.
+ *  - A context is not thread-safe: one thread at a time per context.
+ */
+#ifndef CALIB_H
+#define CALIB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    CALIB_OK = 0,
+    CALIB_EINVAL = -1,   /* bad argument: size, index, layout, non-positive rho, ... */
+    CALIB_ERANK = -2,    /* P < M or sum_i b_i b_i^T singular (Section 3, "P >= F") */
+    CALIB_ENOMEM = -3,   /* device or host allocation failed */
+    CALIB_ECUDA = -4,    /* a CUDA runtime call failed (message names it) */
+    CALIB_ETIMEOUT = -5, /* a bounded wait inside a kernel gave up; results are invalid */
+    CALIB_ENUMERIC = -6, /* non-finite input data */
+    CALIB_ESTATE = -7    /* call order: e.g. calib_admm_iter before any data was set */
+};
+
+typedef struct calib_ctx calib_ctx;
+
+typedef struct {
+    int n_intervals;                   /* I >= 1 (default 1) */
+    int n_samples;                     /* T >= 1: samples per agent when samples_per_agent is NULL */
+    const int32_t* samples_per_agent;  /* [A] samples of each agent, or NULL (host pointer, copied) */
+    int n_lm;                          /* LM steps per J-update (default 10) */
+    int n_cg;                          /* PCG steps per LM step (default 4) */
+    int chunk_diagonals;               /* baseline diagonals per CTA in the sweeps; 0 = automatic */
+    void* cuda_stream;                 /* cudaStream_t to run on; NULL = the library creates one */
+} calib_options;
+
+/* One record per C-ADMM iteration (Section 4 definitions, summed/averaged over all intervals):
+ *  primal     mean over agents i and directions k of ||J_ik - B_i Z_k|| / sqrt(4N)
+ *  dual       mean over intervals and directions of ||Z_k^{n+1} - Z_k^n|| / sqrt(4MN)
+ *  objective  sum_i L_i(J_i^{n+1}, Z^{n+1}, Y_i^{n+1})
+ *  resid_norm sqrt(sum_i g_i(J_i^{n+1}))                                              */
+typedef struct {
+    double primal;
+    double dual;
+    double objective;
+    double resid_norm;
+} calib_stats;
+
+/* Fill *opt with the defaults listed above. */
+void calib_default_options(calib_options* opt);
+
+/* Create a context for a fixed problem shape (Section 3 problem statement, Eq. hidden,
+ * Eq. poly, Eq. Zest).
+ *  n_stations N in [2, 256]; n_baselines B in [1, N(N-1)/2];
+ *  pq        [B][2] int32 station pairs with 0 <= p < q < N, no duplicates (host);
+ *  n_dirs    K in [1, 16];   n_freqs P >= 1;   freqs_hz [P] (host; stored for calib_predict);
+ *  n_basis   M in [1, 16] with P >= M;  basis [P][M] row-major b_l(f_i) (host, float64);
+ *  rho       [K] per-direction regularisation, each > 0 (Section 3) (host);
+ *  opt       may be NULL (defaults).
+ * Computes (sum_i b_i b_i^T)^-1 in float64; returns CALIB_ERANK when it does not exist.
+ * The state starts cold: J = identity blocks, Z = Y = 0 (Section 3, initialisation). */
+int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* pq,
+               int n_dirs, int n_freqs, const double* freqs_hz, int n_basis,
+               const double* basis, const double* rho, const calib_options* opt);
+
+/* Load observed data (Eq. vispq).
+ *  vis   c64, agent-major packed [A][B][T_a][2][2] (the 2x2 block row-major: XX XY YX YY);
+ *  coh   c64 [A][B][T_a][K] scalar coherencies c with C = c I_2, or NULL when calib_predict
+ *        will supply them;
+ *  flags uint8 [A][B], 1 = exclude this baseline of this agent from g (host or device per
+ *        ptr_kind), or NULL = nothing flagged. Flags are fixed at the first call.
+ * Rejects non-finite visibilities (CALIB_ENUMERIC) when ptr_kind is 0. */
+int calib_set_data(calib_ctx* ctx, const void* vis, const void* coh, const uint8_t* flags, int ptr_kind);
+
+/* Predict the scalar coherencies of point-source clusters (Eq. coh) on the GPU.
+ *  uvw_m  float64 [I][Tmax][N][3] per-station (u,v,w) in metres (agent a uses the first T_a
+ *         samples of its interval);  Tmax = max_a T_a;
+ *  sky    float64 [K][S][4] per cluster: l, m (direction cosines), I0 (flux at f0_hz), alpha;
+ *  f0_hz  reference frequency of the spectral indices.
+ * Phase reading: c_pq = sum_s I0_s (f/f0)^alpha_s exp(i phi), phi = -2 pi (f/c)
+ * (u_pq l + v_pq m + w_pq (sqrt(1-l^2-m^2)-1)), (u,v,w)_pq = (u,v,w)_p - (u,v,w)_q.
+ * Turns are formed in float64 per station and reduced to [-1/2, 1/2) before float32
+ * sincospi. Replaces any coherencies given to calib_set_data. */
+int calib_predict(calib_ctx* ctx, const double* uvw_m, const double* sky, int n_src,
+                  double f0_hz, int ptr_kind);
+
+/* Copy the coherencies in use out in the calib_set_data layout [A][B][T_a][K] c64
+ * (flagged baselines read as 0). */
+int calib_get_coherencies(calib_ctx* ctx, void* coh, int ptr_kind);
+
+/* Cold start: J = identity blocks, Z = Y = 0; the next iteration applies the first-iteration
+ * gauge projection (Section 3, initialisation). */
+int calib_reset(calib_ctx* ctx);
+
+/* Set J (c64 [A][K][N][2][2]) as the starting point of the next J-update, for a warm start
+ * from a previous solution interval (Section 3, initialisation). Z and Y are unchanged. */
+int calib_set_initial(calib_ctx* ctx, const void* J0, int ptr_kind);
+
+/* Set the consensus state: Z c128 [I][K][M][N][2][2] and Y c64 [A][K][N][2][2] (either may
+ * be NULL = zero). B_i Z is recomputed. A state set this way is warm: no gauge projection.
+ * With calib_get_solutions this is checkpoint and resume. */
+int calib_set_consensus(calib_ctx* ctx, const void* Z, const void* Y, int ptr_kind);
+
+/* Run n_iters C-ADMM iterations (Eq. M1-M3). If hist is not NULL it receives n_iters
+ * records (host memory, written before return). Returns CALIB_ETIMEOUT if a bounded
+ * in-kernel wait gave up. */
+int calib_admm_iter(calib_ctx* ctx, int n_iters, calib_stats* hist);
+
+/* Copy out J c64 [A][K][N][2][2], Z c128 [I][K][M][N][2][2], Y c64 [A][K][N][2][2].
+ * Any pointer may be NULL. */
+int calib_get_solutions(calib_ctx* ctx, void* J, void* Z, void* Y, int ptr_kind);
+
+/* Per-agent L_i and g_i after the last iteration, float64 [A] each (host). Either may be NULL. */
+int calib_get_agent_objective(calib_ctx* ctx, double* L, double* g);
+
+/* Evaluate the augmented Lagrangian and its gradient at a given J (c64 [A][K][N][2][2])
+ * with the context's current Z and Y: L float64 [A], g float64 [A] (either may be NULL),
+ * grad c64 [A][K][N][2][2] = grad_i(L_i, J) of Eq. gradL (gradient w.r.t. the inner
+ * product h of Eq. inprod; the real-coordinate gradient is twice this). Does not change
+ * the iteration state. L and g are host arrays when ptr_kind is 0, else device. */
+int calib_eval(calib_ctx* ctx, const void* J, double* L, double* g, void* grad, int ptr_kind);
+
+/* Gauss-Newton Hessian-vector product of L_i at J along eta (Eq. HessL with the GN part of
+ * Hess g): out c64 [A][K][N][2][2]. Inputs and output as in calib_eval. */
+int calib_hessvec(calib_ctx* ctx, const void* J, const void* eta, void* out, int ptr_kind);
+
+/* Wait until all work queued on the library stream has finished. */
+int calib_sync(calib_ctx* ctx);
+
+/* Per-kernel timing over the following calib_admm_iter calls (CUDA events recorded
+ * on the library stream around every launch of the sweep kernels when enabled).
+ * names/ms/launches receive up to cap entries; returns the number of kernel kinds. */
+int calib_profile_enable(calib_ctx* ctx, int on);
+int calib_profile_read(calib_ctx* ctx, int cap, const char** names, double* total_ms,
+                       long long* launches, double* bytes_per_launch);
+
+/* Number of kernels this context has launched since creation (all kinds). */
+long long calib_launch_count(calib_ctx* ctx);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* calib_last_error(void);
+
+/* Free the context and all device memory it owns. NULL is allowed. */
+void calib_destroy(calib_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CALIB_H */

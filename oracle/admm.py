@@ -113,8 +113,8 @@ def grad_data(J, V, C, pq) -> np.ndarray:
     p, q = pq[:, 0], pq[:, 1]
     R = residual(J, V, C, pq)
     G = np.zeros_like(J)
-    to_p = -np.einsum("btk,btij,kbjl->kbil", np.conj(C), R, J[:, q])
-    to_q = -np.einsum("btk,btij,kbjl->kbil", C, herm(R), J[:, p])
+    to_p = -np.einsum("btk,btij,kbjl->kbil", np.conj(C), R, J[:, q], optimize=True)
+    to_q = -np.einsum("btk,btij,kbjl->kbil", C, herm(R), J[:, p], optimize=True)
     np.add.at(G, (slice(None), p), to_p)
     np.add.at(G, (slice(None), q), to_q)
     return G
@@ -138,8 +138,8 @@ def hess_gn(J, eta, C, pq) -> np.ndarray:
     Q = np.matmul(eta[:, p], herm(J[:, q])) + np.matmul(J[:, p], herm(eta[:, q]))  # [K,B,2,2]
     dM = np.einsum("btk,kbij->btij", C, Q)
     H = np.zeros_like(J)
-    to_p = np.einsum("btk,btij,kbjl->kbil", np.conj(C), dM, J[:, q])
-    to_q = np.einsum("btk,btij,kbjl->kbil", C, herm(dM), J[:, p])
+    to_p = np.einsum("btk,btij,kbjl->kbil", np.conj(C), dM, J[:, q], optimize=True)
+    to_q = np.einsum("btk,btij,kbjl->kbil", C, herm(dM), J[:, p], optimize=True)
     np.add.at(H, (slice(None), p), to_p)
     np.add.at(H, (slice(None), q), to_q)
     return H

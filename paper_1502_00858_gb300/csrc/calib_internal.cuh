@@ -1,0 +1,148 @@
+// Internal declarations shared by the CUDA translation units of libcalib.so.
+//
+// Device data layout (all float32 unless noted; "block" = one 2x2 complex matrix = 8 floats):
+//   J, Jt, Y, BZ, gradg, gradg_t, grad, x, r, z, p   [A][K][N][8]
+//   Gm        [A][K][N][4]   Jacobi blocks G_pk (Hermitian): g00, g11, re g01, im g01
+//   part      [A][n_chunks][K][N][8]  per-CTA partial station sums of a baseline sweep
+//   part_cost [A][n_chunks]  float64 partial data cost
+//   Z, Zprev  [I][K][M][N][8] float64
+//
+// Baselines are re-laid out per agent by circulant diagonal: diagonal d (1 <= d <= N/2) holds
+// the pairs (i, (i+d) mod N); within one diagonal every station is the first element of at most
+// one pair and the second element of at most one pair, which makes the per-station reductions
+// of the sweeps conflict-free. Data of a pair stored "reversed" (user pair (p,q) held as (q,p))
+// is conjugate-transposed (V) / conjugated (c) on ingestion, so kernels never see orientation.
+//   V block of (agent, diagonal): [T_a][n_pad][4] float2 (32 B per slot and sample)
+//   C block of (agent, diagonal): [T_a][n_pad][K] float2
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace calib {
+
+constexpr int MAX_N = 256;
+constexpr int MAX_K = 16;
+constexpr int MAX_M = 16;
+
+// Budget of a bounded in-kernel wait, in SM clock cycles (about one second at 2 GHz).
+constexpr long long WAIT_BUDGET_CYCLES = 2000000000LL;
+
+enum StatusBits : int { STATUS_TIMEOUT = 1, STATUS_NONFINITE = 2 };
+
+struct DiagDesc {     // one per (agent, diagonal)
+    long long voff;   // float2 offset of the V block
+    long long coff;   // float2 offset of the C block
+    int slot_off;     // global index of the first slot of this diagonal in the slot arrays
+    int n;            // active (unflagged) slots
+    int n_pad;        // padded slot count (multiple of 4, >= n)
+    int pad_;
+};
+
+struct AgentState {   // per-agent scalars
+    double L, g;      // augmented Lagrangian and data cost at the current J
+    double L_t, g_t;  // at the LM trial point
+    double rz;        // PCG r.z
+    double pred;      // predicted decrease of the LM step
+    double mu, nu;    // LM damping
+    int cg_stop;      // PCG stopped (r.z <= 0 or p.Ap <= 0)
+    int accepted;     // LM steps accepted (cumulative)
+    int rejected;     // LM steps rejected (cumulative)
+    int pad_;
+};
+
+// Arguments of a baseline sweep (residual/gradient pass or Gauss-Newton Hessian-vector pass).
+struct SweepArgs {
+    const float2* V;        // interleaved visibilities (internal layout)
+    const float2* C;        // coherencies (internal layout)
+    const DiagDesc* desc;   // [A][D]
+    const int* slot;        // per slot: first | second << 8
+    const int* T;           // [A] samples per agent
+    const float* J;         // [A][K][N][8] operating point
+    const float* eta;       // [A][K][N][8] direction (Hessian pass) or LM step x (trial pass)
+    float* part;            // [A][n_chunks][K][N][8]
+    double* part_cost;      // [A][n_chunks] (residual and trial passes)
+    double* part_dcost;     // [A][n_chunks] decrease of the data cost (trial pass)
+    int* status;            // status bits, set on a timed-out wait
+    int A, N, K, D, n_chunks, chunk_diags, TT, slots_max;
+};
+
+struct LMArgs {
+    const float* part; const double* part_cost; const double* part_dcost; int n_chunks;
+    float* J; float* Jt; const float* Y; const float* BZ;
+    float* gradg; float* grad; float* x; float* r; float* z; float* p; float* Ap;
+    float* Gm;
+    AgentState* st;
+    const float* rho;       // [K]
+    const DiagDesc* desc; const int* slot; const float* spow;   // for the Jacobi blocks
+    int A, N, K, D;
+    double tau;
+};
+
+struct ConsArgs {
+    float* J; float* gradg; float* Gm; float* Y; float* BZ;
+    double* Z; double* Zprev;
+    const double* basis;    // [P][M]
+    const double* Pinv;     // [M][M] (sum_i b_i b_i^T)^-1
+    const float* rho;       // [K]
+    AgentState* st;
+    double* prim;           // [A][K] ||J_ik - B_i Z_k||
+    double* stats;          // [max_iters][4]
+    int* iter_counter;
+    int A, I, P, M, N, K, max_iters;
+};
+
+// ---- launchers (sweep.cu)
+enum SweepMode : int { SWEEP_RESIDUAL = 0, SWEEP_HESSVEC = 1, SWEEP_TRIAL = 2 };
+cudaError_t launch_sweep(const SweepArgs& a, int mode, cudaStream_t s);
+size_t sweep_smem_bytes(int N, int K, bool two_vectors);
+int sweep_tile_samples(int slots_max, int K, bool hessvec);
+int sweep_threads(int slots_max);
+
+// ---- launchers (lm.cu)
+enum LMEvalMode : int { LM_BEGIN_FROM_PARTIALS = 0, LM_BEGIN_REUSE = 1, LM_ACCEPT = 2 };
+cudaError_t launch_lm_eval(const LMArgs& a, int mode, cudaStream_t s);
+cudaError_t launch_cg_step(const LMArgs& a, cudaStream_t s);
+cudaError_t launch_lm_trial(const LMArgs& a, cudaStream_t s);
+cudaError_t launch_eval_output(const LMArgs& a, float* grad_out, double* L_out, double* g_out, cudaStream_t s);
+cudaError_t launch_hv_output(const LMArgs& a, float* out, cudaStream_t s);
+
+// ---- launchers (consensus.cu)
+cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s);
+cudaError_t launch_zupdate(const ConsArgs& a, cudaStream_t s);
+cudaError_t launch_yupdate(const ConsArgs& a, cudaStream_t s);
+cudaError_t launch_stats(const ConsArgs& a, cudaStream_t s);
+cudaError_t launch_bz_only(const ConsArgs& a, cudaStream_t s);
+cudaError_t launch_identity(float* J, long long n_blocks, cudaStream_t s);
+
+// ---- launchers (data.cu)
+struct IngestArgs {
+    const float2* src;          // user layout [A][B][T_a][w] (w = 4 for V, K for C)
+    const long long* src_off;   // [A] float2 offset of each agent's [B][T_a][w] block
+    const uint8_t* flags;       // unused here (slots already compacted)
+    float2* dst;
+    const DiagDesc* desc; const int* slot; const int* slot_b; const int* T;
+    int A, D, K, is_vis;
+};
+cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t s);
+cudaError_t launch_extract_coh(const IngestArgs& a, float2* user_dst, cudaStream_t s);
+struct PredictArgs {
+    const double* uvw;      // [I][Tmax][N][3]
+    const double* sky;      // [K][S][4]
+    const double* freqs;    // [P]
+    double f0;
+    float2* C;
+    const DiagDesc* desc; const int* slot; const int* T;
+    int A, P, N, K, S, D, Tmax;
+};
+cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s);
+cudaError_t launch_coh_power(const float2* C, const DiagDesc* desc, const int* T, float* spow,
+                             int A, int D, int K, cudaStream_t s);
+cudaError_t launch_check_finite(const float* x, long long n, int* status, cudaStream_t s);
+
+// One-time kernel attribute set-up (dynamic shared memory limits); call before any capture.
+cudaError_t prepare_sweep_kernels();
+cudaError_t prepare_lm_kernels();
+cudaError_t prepare_data_kernels();
+
+}  // namespace calib

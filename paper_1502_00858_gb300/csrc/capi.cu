@@ -1,0 +1,912 @@
+// C ABI of libcalib.so (declared in include/calib.h): context, device layout, the C-ADMM
+// iteration schedule (Section 3, steps D1-D3) captured into CUDA graphs, and the data paths.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "calib.h"
+#include "calib_internal.cuh"
+
+using namespace calib;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(expr)                                                                                \
+    do {                                                                                        \
+        cudaError_t _e = (expr);                                                                \
+        if (_e != cudaSuccess) return fail(CALIB_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+struct ProfPair {
+    cudaEvent_t a, b;
+    int kind;  // 0 residual or trial sweep, 1 Hessian sweep
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
+    std::vector<ProfPair> prof;
+};
+
+}  // namespace
+
+struct calib_ctx {
+    int dev = 0;
+    int N = 0, B = 0, K = 0, P = 0, M = 0, I = 0, A = 0, D = 0;
+    int n_lm = 10, n_cg = 4, chunk_diags = 1, n_chunks = 1, slots_max = 4;
+    int TT_res = 1, TT_hv = 1;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+
+    std::vector<int32_t> pq;
+    std::vector<double> freqs, basis, rho, Pinv;
+    std::vector<float> rho_f;
+    std::vector<int> T;
+    std::vector<long long> vis_off, coh_off;   // user layout offsets per agent (float2 units)
+    long long user_v = 0, user_c = 0;           // user layout totals (float2)
+
+    // layout (depends on flags)
+    std::vector<DiagDesc> desc_h;
+    std::vector<int> slot_h, slot_b_h;
+    long long int_v = 0, int_c = 0;             // internal totals (float2)
+    double alg_bytes_res = 0, alg_bytes_hv = 0; // algorithmic bytes per sweep launch
+    std::vector<uint8_t> flags_h;
+
+    // device
+    float2 *V = nullptr, *C = nullptr;
+    DiagDesc* desc = nullptr;
+    int *slot = nullptr, *slot_b = nullptr, *T_d = nullptr;
+    float* spow = nullptr;
+    long long *vis_off_d = nullptr, *coh_off_d = nullptr;
+    float *J = nullptr, *Jt = nullptr, *Y = nullptr, *BZ = nullptr, *gradg = nullptr, *grad = nullptr;
+    float *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *Gm = nullptr;
+    float *evJ = nullptr, *evE = nullptr, *evOut = nullptr;
+    float* part = nullptr;
+    double* part_cost = nullptr;
+    double* part_dcost = nullptr;
+    double *Z = nullptr, *Zprev = nullptr, *basis_d = nullptr, *Pinv_d = nullptr, *freqs_d = nullptr;
+    float* rho_d = nullptr;
+    AgentState* st = nullptr;
+    double* prim = nullptr;
+    double* stats = nullptr;
+    int max_iters = 0;
+    int* iter_counter = nullptr;
+    int* status = nullptr;
+    double* evL = nullptr;
+    double* evG = nullptr;
+    void* staging = nullptr;
+    size_t staging_bytes = 0;
+
+    bool data_set = false, coh_set = false;
+    bool cold = true, need_eval = true;
+
+    std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;
+    long long launches = 0;
+    bool profiling = false;
+    double prof_ms[2] = {0, 0};
+    long long prof_n[2] = {0, 0};
+};
+
+namespace {
+
+SweepArgs sweep_args(calib_ctx* c, int mode, const float* J, const float* eta) {
+    const bool hv = mode == SWEEP_HESSVEC;
+    SweepArgs a{};
+    a.V = c->V;
+    a.C = c->C;
+    a.desc = c->desc;
+    a.slot = c->slot;
+    a.T = c->T_d;
+    a.J = J;
+    a.eta = eta;
+    a.part = c->part;
+    a.part_cost = c->part_cost;
+    a.part_dcost = c->part_dcost;
+    a.status = c->status;
+    a.A = c->A;
+    a.N = c->N;
+    a.K = c->K;
+    a.D = c->D;
+    a.n_chunks = c->n_chunks;
+    a.chunk_diags = c->chunk_diags;
+    a.TT = hv ? c->TT_hv : c->TT_res;
+    a.slots_max = c->slots_max;
+    return a;
+}
+
+LMArgs lm_args(calib_ctx* c) {
+    LMArgs a{};
+    a.part = c->part;
+    a.part_cost = c->part_cost;
+    a.part_dcost = c->part_dcost;
+    a.n_chunks = c->n_chunks;
+    a.J = c->J;
+    a.Jt = c->Jt;
+    a.Y = c->Y;
+    a.BZ = c->BZ;
+    a.gradg = c->gradg;
+    a.grad = c->grad;
+    a.x = c->x;
+    a.r = c->r;
+    a.z = c->z;
+    a.p = c->p;
+    a.Ap = c->Ap;
+    a.Gm = c->Gm;
+    a.st = c->st;
+    a.rho = c->rho_d;
+    a.desc = c->desc;
+    a.slot = c->slot;
+    a.spow = c->spow;
+    a.A = c->A;
+    a.N = c->N;
+    a.K = c->K;
+    a.D = c->D;
+    a.tau = 1e-3;
+    return a;
+}
+
+ConsArgs cons_args(calib_ctx* c) {
+    ConsArgs a{};
+    a.J = c->J;
+    a.gradg = c->gradg;
+    a.Gm = c->Gm;
+    a.Y = c->Y;
+    a.BZ = c->BZ;
+    a.Z = c->Z;
+    a.Zprev = c->Zprev;
+    a.basis = c->basis_d;
+    a.Pinv = c->Pinv_d;
+    a.rho = c->rho_d;
+    a.st = c->st;
+    a.prim = c->prim;
+    a.stats = c->stats;
+    a.iter_counter = c->iter_counter;
+    a.A = c->A;
+    a.I = c->I;
+    a.P = c->P;
+    a.M = c->M;
+    a.N = c->N;
+    a.K = c->K;
+    a.max_iters = c->max_iters;
+    return a;
+}
+
+// Invert the M x M symmetric matrix sum_i b_i b_i^T (Eq. Zest) by Gauss-Jordan with partial pivoting.
+bool invert_gram(const std::vector<double>& basis, int P, int M, std::vector<double>& inv) {
+    std::vector<double> a((size_t)M * 2 * M, 0.0);
+    double scale = 0.0;
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) {
+            double s = 0.0;
+            for (int f = 0; f < P; ++f) s += basis[(size_t)f * M + i] * basis[(size_t)f * M + j];
+            a[(size_t)i * 2 * M + j] = s;
+            scale = std::max(scale, std::fabs(s));
+        }
+    for (int i = 0; i < M; ++i) a[(size_t)i * 2 * M + M + i] = 1.0;
+    for (int col = 0; col < M; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < M; ++r)
+            if (std::fabs(a[(size_t)r * 2 * M + col]) > std::fabs(a[(size_t)piv * 2 * M + col])) piv = r;
+        if (!(std::fabs(a[(size_t)piv * 2 * M + col]) > 1e-13 * scale)) return false;
+        if (piv != col)
+            for (int j = 0; j < 2 * M; ++j) std::swap(a[(size_t)piv * 2 * M + j], a[(size_t)col * 2 * M + j]);
+        const double d = a[(size_t)col * 2 * M + col];
+        for (int j = 0; j < 2 * M; ++j) a[(size_t)col * 2 * M + j] /= d;
+        for (int r = 0; r < M; ++r) {
+            if (r == col) continue;
+            const double f = a[(size_t)r * 2 * M + col];
+            if (f == 0.0) continue;
+            for (int j = 0; j < 2 * M; ++j) a[(size_t)r * 2 * M + j] -= f * a[(size_t)col * 2 * M + j];
+        }
+    }
+    inv.assign((size_t)M * M, 0.0);
+    for (int i = 0; i < M; ++i)
+        for (int j = 0; j < M; ++j) inv[(size_t)i * M + j] = a[(size_t)i * 2 * M + M + j];
+    return true;
+}
+
+void free_layout(calib_ctx* c) {
+    cudaFree(c->V); c->V = nullptr;
+    cudaFree(c->C); c->C = nullptr;
+    cudaFree(c->desc); c->desc = nullptr;
+    cudaFree(c->slot); c->slot = nullptr;
+    cudaFree(c->slot_b); c->slot_b = nullptr;
+    cudaFree(c->spow); c->spow = nullptr;
+}
+
+void clear_graphs(calib_ctx* c) {
+    for (auto& kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto& pp : kv.second.prof) {
+            cudaEventDestroy(pp.a);
+            cudaEventDestroy(pp.b);
+        }
+    }
+    c->graphs.clear();
+}
+
+// Circulant-diagonal slot layout for the given flags (see calib_internal.cuh).
+int build_layout(calib_ctx* c, const uint8_t* flags) {
+    const int N = c->N, D = c->D, A = c->A, K = c->K;
+    std::vector<int> pair_b((size_t)N * N, -1);
+    for (int b = 0; b < c->B; ++b) pair_b[(size_t)c->pq[2 * b] * N + c->pq[2 * b + 1]] = b;
+    c->desc_h.assign((size_t)A * D, DiagDesc{});
+    c->slot_h.clear();
+    c->slot_b_h.clear();
+    long long voff = 0, coff = 0;
+    int smax = 4;
+    double alg_res = 0, alg_hv = 0;
+    for (int a = 0; a < A; ++a) {
+        for (int d = 1; d <= D; ++d) {
+            DiagDesc& dd = c->desc_h[(size_t)a * D + d - 1];
+            dd.slot_off = (int)c->slot_h.size();
+            const int n_i = (2 * d == N) ? N / 2 : N;
+            int n = 0;
+            for (int i = 0; i < n_i; ++i) {
+                const int j = (i + d) % N;
+                const int p = std::min(i, j), q = std::max(i, j);
+                const int b = pair_b[(size_t)p * N + q];
+                if (b < 0) continue;
+                if (flags && flags[(size_t)a * c->B + b]) continue;
+                const int rev = (i > j) ? 1 : 0;
+                c->slot_h.push_back(i | (j << 8) | (rev << 16));
+                c->slot_b_h.push_back(b);
+                ++n;
+            }
+            dd.n = n;
+            dd.n_pad = (n + 3) / 4 * 4;
+            dd.voff = voff;
+            dd.coff = coff;
+            voff += (long long)c->T[a] * dd.n_pad * 4;
+            coff += (long long)c->T[a] * dd.n_pad * K;
+            smax = std::max(smax, dd.n_pad);
+            alg_res += (double)n * c->T[a] * (32.0 + 8.0 * K);
+            alg_hv += (double)n * c->T[a] * (8.0 * K);
+        }
+    }
+    c->int_v = voff;
+    c->int_c = coff;
+    c->slots_max = smax;
+    c->alg_bytes_res = alg_res;
+    c->alg_bytes_hv = alg_hv;
+    c->TT_res = sweep_tile_samples(smax, K, false);
+    c->TT_hv = sweep_tile_samples(smax, K, true);
+    if (sweep_threads(smax) > 512) return fail(CALIB_EINVAL, "too many stations for one CTA per diagonal");
+    if ((size_t)3 * 24 * 1024 + sweep_smem_bytes(N, K, true) + 4096 > 200 * 1024)
+        return fail(CALIB_EINVAL, "N*K too large for the sweep kernels' shared memory");
+
+    free_layout(c);
+    CK(dalloc(&c->V, (size_t)c->int_v));
+    CK(dalloc(&c->C, (size_t)c->int_c));
+    CK(dalloc(&c->desc, c->desc_h.size()));
+    CK(dalloc(&c->slot, c->slot_h.size()));
+    CK(dalloc(&c->slot_b, c->slot_b_h.size()));
+    CK(dalloc(&c->spow, c->slot_h.size() * (size_t)K));
+    CK(cudaMemcpy(c->desc, c->desc_h.data(), c->desc_h.size() * sizeof(DiagDesc), cudaMemcpyHostToDevice));
+    if (!c->slot_h.empty()) {
+        CK(cudaMemcpy(c->slot, c->slot_h.data(), c->slot_h.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->slot_b, c->slot_b_h.data(), c->slot_b_h.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemset(c->V, 0, (size_t)std::max(1LL, c->int_v) * sizeof(float2)));
+    CK(cudaMemset(c->C, 0, (size_t)std::max(1LL, c->int_c) * sizeof(float2)));
+    clear_graphs(c);
+    c->data_set = false;
+    c->coh_set = false;
+    return CALIB_OK;
+}
+
+int ensure_staging(calib_ctx* c, size_t bytes) {
+    if (c->staging_bytes >= bytes) return CALIB_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->staging);
+    c->staging = nullptr;
+    c->staging_bytes = 0;
+    CK(cudaMalloc(&c->staging, bytes));
+    c->staging_bytes = bytes;
+    return CALIB_OK;
+}
+
+// Device pointer to caller data: device pointers pass through, host data is copied to staging.
+int stage_in(calib_ctx* c, const void* src, size_t bytes, int ptr_kind, const void** dev, size_t staging_off = 0) {
+    if (ptr_kind == 1) {
+        *dev = src;
+        return CALIB_OK;
+    }
+    int rc = ensure_staging(c, staging_off + bytes);
+    if (rc) return rc;
+    char* d = static_cast<char*>(c->staging) + staging_off;
+    CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    *dev = d;
+    return CALIB_OK;
+}
+
+int copy_out(calib_ctx* c, void* dst, const void* dev_src, size_t bytes, int ptr_kind) {
+    if (!dst) return CALIB_OK;
+    CK(cudaMemcpyAsync(dst, dev_src, bytes, ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    return CALIB_OK;
+}
+
+int check_status(calib_ctx* c) {
+    int st = 0;
+    CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & STATUS_TIMEOUT) return fail(CALIB_ETIMEOUT, "a bounded in-kernel wait timed out");
+    if (st & STATUS_NONFINITE) return fail(CALIB_ENUMERIC, "input data contain non-finite values");
+    return CALIB_OK;
+}
+
+// ---------------------------------------------------------------------------- schedule
+
+struct Enq {
+    calib_ctx* c;
+    GraphEntry* ge;
+    cudaError_t err = cudaSuccess;
+    void ok(cudaError_t e) {
+        if (err == cudaSuccess && e != cudaSuccess) err = e;
+        ge->kernels += 1;
+    }
+    void sweep(int mode, const float* J, const float* eta) {
+        ProfPair pp{};
+        const bool prof = c->profiling;
+        if (prof) {
+            cudaEventCreate(&pp.a);
+            cudaEventCreate(&pp.b);
+            pp.kind = mode == SWEEP_HESSVEC ? 1 : 0;
+            cudaEventRecordWithFlags(pp.a, c->stream, cudaEventRecordExternal);
+        }
+        ok(launch_sweep(sweep_args(c, mode, J, eta), mode, c->stream));
+        if (prof) {
+            cudaEventRecordWithFlags(pp.b, c->stream, cudaEventRecordExternal);
+            ge->prof.push_back(pp);
+        }
+    }
+};
+
+void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
+    calib_ctx* c = q.c;
+    const LMArgs la = lm_args(c);
+    const ConsArgs ca = cons_args(c);
+    if (eval_first) {
+        q.sweep(SWEEP_RESIDUAL, c->J, nullptr);
+        q.ok(launch_lm_eval(la, LM_BEGIN_FROM_PARTIALS, c->stream));
+    } else {
+        q.ok(launch_lm_eval(la, LM_BEGIN_REUSE, c->stream));
+    }
+    for (int l = 0; l < c->n_lm; ++l) {
+        for (int k = 0; k < c->n_cg; ++k) {
+            q.sweep(SWEEP_HESSVEC, c->J, c->p);
+            q.ok(launch_cg_step(la, c->stream));
+        }
+        q.ok(launch_lm_trial(la, c->stream));
+        q.sweep(SWEEP_TRIAL, c->J, c->x);
+        q.ok(launch_lm_eval(la, LM_ACCEPT, c->stream));
+    }
+    if (gauge) q.ok(launch_gauge(ca, c->stream));
+    q.ok(launch_zupdate(ca, c->stream));
+    q.ok(launch_yupdate(ca, c->stream));
+    q.ok(launch_stats(ca, c->stream));
+}
+
+int ensure_stats(calib_ctx* c, int n) {
+    if (c->max_iters >= n) return CALIB_OK;
+    CK(cudaStreamSynchronize(c->stream));
+    cudaFree(c->stats);
+    c->stats = nullptr;
+    CK(dalloc(&c->stats, (size_t)n * 4));
+    c->max_iters = n;
+    clear_graphs(c);  // graphs hold the old pointer and capacity
+    return CALIB_OK;
+}
+
+bool valid_kind(int k) { return k == 0 || k == 1; }
+
+}  // namespace
+
+extern "C" {
+
+void calib_default_options(calib_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->n_intervals = 1;
+    opt->n_samples = 1;
+    opt->samples_per_agent = nullptr;
+    opt->n_lm = 10;
+    opt->n_cg = 4;
+    opt->chunk_diagonals = 0;
+    opt->cuda_stream = nullptr;
+}
+
+int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* pq, int n_dirs, int n_freqs,
+               const double* freqs_hz, int n_basis, const double* basis, const double* rho,
+               const calib_options* opt_in) {
+    if (!out) return fail(CALIB_EINVAL, "out is NULL");
+    *out = nullptr;
+    calib_options opt;
+    calib_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    const int N = n_stations, B = n_baselines, K = n_dirs, P = n_freqs, M = n_basis;
+    if (N < 2 || N > 128) return fail(CALIB_EINVAL, "n_stations must be in [2, 128]");
+    if (B < 1 || B > N * (N - 1) / 2) return fail(CALIB_EINVAL, "n_baselines must be in [1, N(N-1)/2]");
+    if (K < 1 || K > MAX_K) return fail(CALIB_EINVAL, "n_dirs must be in [1, 16]");
+    if (P < 1) return fail(CALIB_EINVAL, "n_freqs must be >= 1");
+    if (M < 1 || M > MAX_M) return fail(CALIB_EINVAL, "n_basis must be in [1, 16]");
+    if (!pq || !freqs_hz || !basis || !rho) return fail(CALIB_EINVAL, "pq, freqs_hz, basis and rho are required");
+    if (P < M) return fail(CALIB_ERANK, "need at least as many frequencies as basis terms (P >= M)");
+    if (opt.n_intervals < 1) return fail(CALIB_EINVAL, "n_intervals must be >= 1");
+    if (opt.n_lm < 1 || opt.n_cg < 1) return fail(CALIB_EINVAL, "n_lm and n_cg must be >= 1");
+    std::vector<char> seen((size_t)N * N, 0);
+    for (int b = 0; b < B; ++b) {
+        const int p = pq[2 * b], q = pq[2 * b + 1];
+        if (p < 0 || q >= N || p >= q) return fail(CALIB_EINVAL, "each pair must satisfy 0 <= p < q < N");
+        if (seen[(size_t)p * N + q]) return fail(CALIB_EINVAL, "duplicate baseline");
+        seen[(size_t)p * N + q] = 1;
+    }
+    for (int k = 0; k < K; ++k)
+        if (!(rho[k] > 0.0) || !std::isfinite(rho[k])) return fail(CALIB_EINVAL, "rho must be finite and > 0");
+    for (int i = 0; i < P * M; ++i)
+        if (!std::isfinite(basis[i])) return fail(CALIB_EINVAL, "basis must be finite");
+    const int A = opt.n_intervals * P;
+    std::vector<int> T(A);
+    for (int a = 0; a < A; ++a) {
+        T[a] = opt.samples_per_agent ? opt.samples_per_agent[a] : opt.n_samples;
+        if (T[a] < 1) return fail(CALIB_EINVAL, "every agent needs at least one sample");
+    }
+    std::vector<double> Pinv;
+    if (!invert_gram(std::vector<double>(basis, basis + (size_t)P * M), P, M, Pinv))
+        return fail(CALIB_ERANK, "sum_i b_i b_i^T is singular");
+
+    calib_ctx* c = new calib_ctx();
+    c->N = N; c->B = B; c->K = K; c->P = P; c->M = M; c->I = opt.n_intervals; c->A = A;
+    c->D = N / 2;
+    c->n_lm = opt.n_lm;
+    c->n_cg = opt.n_cg;
+    c->pq.assign(pq, pq + 2 * (size_t)B);
+    c->freqs.assign(freqs_hz, freqs_hz + P);
+    c->basis.assign(basis, basis + (size_t)P * M);
+    c->rho.assign(rho, rho + K);
+    c->rho_f.resize(K);
+    for (int k = 0; k < K; ++k) c->rho_f[k] = (float)rho[k];
+    c->Pinv = Pinv;
+    c->T = T;
+    c->vis_off.resize(A);
+    c->coh_off.resize(A);
+    long long vo = 0, co = 0;
+    for (int a = 0; a < A; ++a) {
+        c->vis_off[a] = vo;
+        c->coh_off[a] = co;
+        vo += (long long)B * T[a] * 4;
+        co += (long long)B * T[a] * K;
+    }
+    c->user_v = vo;
+    c->user_c = co;
+    if (opt.chunk_diagonals > 0) {
+        c->chunk_diags = std::min(opt.chunk_diagonals, c->D);
+    } else {
+        const int want = std::max(1, std::min(c->D, (1216 + A - 1) / A));
+        c->chunk_diags = (c->D + want - 1) / want;
+    }
+    c->n_chunks = (c->D + c->chunk_diags - 1) / c->chunk_diags;
+
+    auto bail = [&](int rc) { calib_destroy(c); return rc; };
+    if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(fail(CALIB_ECUDA, "no CUDA device"));
+    if (opt.cuda_stream) {
+        c->stream = static_cast<cudaStream_t>(opt.cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(CALIB_ECUDA, "cudaStreamCreate failed"));
+        c->own_stream = true;
+    }
+    cudaError_t pe = prepare_sweep_kernels();
+    if (pe == cudaSuccess) pe = prepare_lm_kernels();
+    if (pe == cudaSuccess) pe = prepare_data_kernels();
+    if (pe != cudaSuccess) return bail(fail(CALIB_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(pe)));
+
+    const size_t vec = (size_t)A * K * N * 8;
+    bool okm = true;
+    for (float** pp : {&c->J, &c->Jt, &c->Y, &c->BZ, &c->gradg, &c->grad, &c->x, &c->r, &c->z, &c->p, &c->Ap,
+                       &c->evJ, &c->evE, &c->evOut})
+        okm = okm && dalloc(pp, vec) == cudaSuccess;
+    okm = okm && dalloc(&c->Gm, (size_t)A * K * N * 4) == cudaSuccess;
+    okm = okm && dalloc(&c->part, (size_t)A * c->n_chunks * K * N * 8) == cudaSuccess;
+    okm = okm && dalloc(&c->part_cost, (size_t)A * c->n_chunks) == cudaSuccess;
+    okm = okm && dalloc(&c->part_dcost, (size_t)A * c->n_chunks) == cudaSuccess;
+    const size_t zs = (size_t)c->I * K * M * N * 8;
+    okm = okm && dalloc(&c->Z, zs) == cudaSuccess && dalloc(&c->Zprev, zs) == cudaSuccess;
+    okm = okm && dalloc(&c->basis_d, (size_t)P * M) == cudaSuccess && dalloc(&c->Pinv_d, (size_t)M * M) == cudaSuccess;
+    okm = okm && dalloc(&c->freqs_d, (size_t)P) == cudaSuccess && dalloc(&c->rho_d, (size_t)K) == cudaSuccess;
+    okm = okm && dalloc(&c->st, (size_t)A) == cudaSuccess && dalloc(&c->prim, (size_t)A * K) == cudaSuccess;
+    okm = okm && dalloc(&c->iter_counter, 1) == cudaSuccess && dalloc(&c->status, 1) == cudaSuccess;
+    okm = okm && dalloc(&c->evL, (size_t)A) == cudaSuccess && dalloc(&c->evG, (size_t)A) == cudaSuccess;
+    okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess;
+    okm = okm && dalloc(&c->vis_off_d, (size_t)A) == cudaSuccess && dalloc(&c->coh_off_d, (size_t)A) == cudaSuccess;
+    if (!okm) return bail(fail(CALIB_ENOMEM, "device allocation failed"));
+    if (ensure_stats(c, 64) != CALIB_OK) return bail(CALIB_ENOMEM);
+    cudaMemcpy(c->basis_d, c->basis.data(), c->basis.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->Pinv_d, c->Pinv.data(), c->Pinv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->freqs_d, c->freqs.data(), c->freqs.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->rho_d, c->rho_f.data(), c->rho_f.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->T_d, c->T.data(), c->T.size() * sizeof(int), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->vis_off_d, c->vis_off.data(), c->vis_off.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->coh_off_d, c->coh_off.data(), c->coh_off.size() * sizeof(long long), cudaMemcpyHostToDevice);
+    cudaMemset(c->status, 0, sizeof(int));
+    cudaMemset(c->st, 0, (size_t)A * sizeof(AgentState));
+    cudaMemset(c->prim, 0, (size_t)A * K * sizeof(double));
+    int rc = build_layout(c, nullptr);
+    if (rc) return bail(rc);
+    rc = calib_reset(c);
+    if (rc) return bail(rc);
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(fail(CALIB_ECUDA, "initialisation failed"));
+    *out = c;
+    return CALIB_OK;
+}
+
+int calib_reset(calib_ctx* c) {
+    if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
+    const size_t vec = (size_t)c->A * c->K * c->N * 8;
+    CK(launch_identity(c->J, (long long)c->A * c->K * c->N, c->stream));
+    CK(cudaMemsetAsync(c->Y, 0, vec * sizeof(float), c->stream));
+    CK(cudaMemsetAsync(c->BZ, 0, vec * sizeof(float), c->stream));
+    const size_t zs = (size_t)c->I * c->K * c->M * c->N * 8;
+    CK(cudaMemsetAsync(c->Z, 0, zs * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(c->Zprev, 0, zs * sizeof(double), c->stream));
+    c->launches += 1;
+    c->cold = true;
+    c->need_eval = true;
+    return CALIB_OK;
+}
+
+int calib_set_data(calib_ctx* c, const void* vis, const void* coh, const uint8_t* flags, int ptr_kind) {
+    if (!c || !vis) return fail(CALIB_EINVAL, "ctx and vis are required");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    if (flags) {
+        std::vector<uint8_t> fh((size_t)c->A * c->B);
+        CK(cudaMemcpy(fh.data(), flags, fh.size(), ptr_kind == 1 ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+        if (fh != c->flags_h) {
+            CK(cudaStreamSynchronize(c->stream));
+            int rc = build_layout(c, fh.data());
+            if (rc) return rc;
+            c->flags_h = fh;
+        }
+    }
+    IngestArgs ia{};
+    ia.desc = c->desc;
+    ia.slot = c->slot;
+    ia.slot_b = c->slot_b;
+    ia.T = c->T_d;
+    ia.A = c->A;
+    ia.D = c->D;
+    ia.K = c->K;
+    const void* dv = nullptr;
+    int rc = stage_in(c, vis, (size_t)c->user_v * sizeof(float2), ptr_kind, &dv);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    CK(launch_check_finite(static_cast<const float*>(dv), c->user_v * 2, c->status, c->stream));
+    ia.src = static_cast<const float2*>(dv);
+    ia.src_off = c->vis_off_d;
+    ia.dst = c->V;
+    ia.is_vis = 1;
+    CK(launch_ingest(ia, c->stream));
+    c->launches += 2;
+    if (coh) {
+        const void* dc = nullptr;
+        rc = stage_in(c, coh, (size_t)c->user_c * sizeof(float2), ptr_kind, &dc);
+        if (rc) return rc;
+        CK(launch_check_finite(static_cast<const float*>(dc), c->user_c * 2, c->status, c->stream));
+        ia.src = static_cast<const float2*>(dc);
+        ia.src_off = c->coh_off_d;
+        ia.dst = c->C;
+        ia.is_vis = 0;
+        CK(launch_ingest(ia, c->stream));
+        CK(launch_coh_power(c->C, c->desc, c->T_d, c->spow, c->A, c->D, c->K, c->stream));
+        c->launches += 3;
+        c->coh_set = true;
+    }
+    c->data_set = true;
+    c->need_eval = true;
+    if (ptr_kind == 0) {
+        CK(cudaStreamSynchronize(c->stream));
+        return check_status(c);
+    }
+    return CALIB_OK;
+}
+
+int calib_predict(calib_ctx* c, const double* uvw_m, const double* sky, int n_src, double f0_hz, int ptr_kind) {
+    if (!c || !uvw_m || !sky) return fail(CALIB_EINVAL, "ctx, uvw_m and sky are required");
+    if (n_src < 1) return fail(CALIB_EINVAL, "n_src must be >= 1");
+    if (!(f0_hz > 0)) return fail(CALIB_EINVAL, "f0_hz must be > 0");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    const int Tmax = *std::max_element(c->T.begin(), c->T.end());
+    const size_t ub = (size_t)c->I * Tmax * c->N * 3 * sizeof(double);
+    const size_t sb = (size_t)c->K * n_src * 4 * sizeof(double);
+    const void *du = nullptr, *ds = nullptr;
+    const size_t sky_off = (ub + 255) / 256 * 256;
+    if (ptr_kind == 0) {  // size the staging buffer once: a later resize would free the staged uvw
+        int rc0 = ensure_staging(c, sky_off + sb);
+        if (rc0) return rc0;
+    }
+    int rc = stage_in(c, uvw_m, ub, ptr_kind, &du, 0);
+    if (rc) return rc;
+    rc = stage_in(c, sky, sb, ptr_kind, &ds, sky_off);
+    if (rc) return rc;
+    PredictArgs pa{};
+    pa.uvw = static_cast<const double*>(du);
+    pa.sky = static_cast<const double*>(ds);
+    pa.freqs = c->freqs_d;
+    pa.f0 = f0_hz;
+    pa.C = c->C;
+    pa.desc = c->desc;
+    pa.slot = c->slot;
+    pa.T = c->T_d;
+    pa.A = c->A;
+    pa.P = c->P;
+    pa.N = c->N;
+    pa.K = c->K;
+    pa.S = n_src;
+    pa.D = c->D;
+    pa.Tmax = Tmax;
+    CK(launch_predict(pa, c->stream));
+    CK(launch_coh_power(c->C, c->desc, c->T_d, c->spow, c->A, c->D, c->K, c->stream));
+    c->launches += 2;
+    c->coh_set = true;
+    c->need_eval = true;
+    if (ptr_kind == 0) CK(cudaStreamSynchronize(c->stream));
+    return CALIB_OK;
+}
+
+int calib_get_coherencies(calib_ctx* c, void* coh, int ptr_kind) {
+    if (!c || !coh) return fail(CALIB_EINVAL, "ctx and coh are required");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    if (!c->coh_set) return fail(CALIB_ESTATE, "no coherencies set or predicted yet");
+    const size_t bytes = (size_t)c->user_c * sizeof(float2);
+    void* dst = coh;
+    if (ptr_kind == 0) {
+        int rc = ensure_staging(c, bytes);
+        if (rc) return rc;
+        dst = c->staging;
+    }
+    CK(cudaMemsetAsync(dst, 0, bytes, c->stream));
+    IngestArgs ia{};
+    ia.desc = c->desc;
+    ia.slot = c->slot;
+    ia.slot_b = c->slot_b;
+    ia.T = c->T_d;
+    ia.A = c->A;
+    ia.D = c->D;
+    ia.K = c->K;
+    ia.src_off = c->coh_off_d;
+    ia.dst = c->C;
+    CK(launch_extract_coh(ia, static_cast<float2*>(dst), c->stream));
+    c->launches += 1;
+    if (ptr_kind == 0) {
+        CK(cudaMemcpyAsync(coh, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return CALIB_OK;
+}
+
+int calib_set_initial(calib_ctx* c, const void* J0, int ptr_kind) {
+    if (!c || !J0) return fail(CALIB_EINVAL, "ctx and J0 are required");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    const size_t bytes = (size_t)c->A * c->K * c->N * 8 * sizeof(float);
+    CK(cudaMemcpyAsync(c->J, J0, bytes, ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    c->need_eval = true;
+    if (ptr_kind == 0) CK(cudaStreamSynchronize(c->stream));
+    return CALIB_OK;
+}
+
+int calib_set_consensus(calib_ctx* c, const void* Zin, const void* Yin, int ptr_kind) {
+    if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    const cudaMemcpyKind kind = ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t zs = (size_t)c->I * c->K * c->M * c->N * 8 * sizeof(double);
+    const size_t ys = (size_t)c->A * c->K * c->N * 8 * sizeof(float);
+    if (Zin) CK(cudaMemcpyAsync(c->Z, Zin, zs, kind, c->stream));
+    else CK(cudaMemsetAsync(c->Z, 0, zs, c->stream));
+    CK(cudaMemcpyAsync(c->Zprev, c->Z, zs, cudaMemcpyDeviceToDevice, c->stream));
+    if (Yin) CK(cudaMemcpyAsync(c->Y, Yin, ys, kind, c->stream));
+    else CK(cudaMemsetAsync(c->Y, 0, ys, c->stream));
+    ConsArgs ca = cons_args(c);
+    ca.prim = nullptr;
+    CK(launch_bz_only(ca, c->stream));
+    c->launches += 1;
+    c->cold = false;
+    c->need_eval = true;
+    if (ptr_kind == 0) CK(cudaStreamSynchronize(c->stream));
+    return CALIB_OK;
+}
+
+int calib_admm_iter(calib_ctx* c, int n_iters, calib_stats* hist) {
+    if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
+    if (n_iters < 1) return fail(CALIB_EINVAL, "n_iters must be >= 1");
+    if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "set visibilities and coherencies first");
+    int rc = ensure_stats(c, n_iters);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(c->iter_counter, 0, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    const auto key = std::make_tuple(n_iters, c->need_eval ? 1 : 0, c->cold ? 1 : 0, c->profiling ? 1 : 0);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        GraphEntry ge;
+        Enq q{c, &ge};
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        for (int n = 0; n < n_iters; ++n) enqueue_iteration(q, n == 0 && c->need_eval, n == 0 && c->cold);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(c->stream, &g);
+        if (q.err != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return fail(CALIB_ECUDA, std::string("kernel launch during capture: ") + cudaGetErrorString(q.err));
+        }
+        CK(ce);
+        cudaError_t ie = cudaGraphInstantiate(&ge.exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(ie);
+        it = c->graphs.emplace(key, ge).first;
+    }
+    CK(cudaGraphLaunch(it->second.exec, c->stream));
+    c->launches += it->second.kernels;
+    c->need_eval = false;
+    c->cold = false;
+    CK(cudaStreamSynchronize(c->stream));
+    rc = check_status(c);
+    if (rc) return rc;
+    if (c->profiling) {
+        for (auto& pp : it->second.prof) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, pp.a, pp.b));
+            c->prof_ms[pp.kind] += ms;
+            c->prof_n[pp.kind] += 1;
+        }
+    }
+    if (hist) {
+        std::vector<double> h((size_t)n_iters * 4);
+        CK(cudaMemcpy(h.data(), c->stats, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        for (int i = 0; i < n_iters; ++i) {
+            hist[i].primal = h[(size_t)i * 4 + 0];
+            hist[i].dual = h[(size_t)i * 4 + 1];
+            hist[i].objective = h[(size_t)i * 4 + 2];
+            hist[i].resid_norm = h[(size_t)i * 4 + 3];
+        }
+    }
+    return CALIB_OK;
+}
+
+int calib_get_solutions(calib_ctx* c, void* J, void* Zo, void* Yo, int ptr_kind) {
+    if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    const size_t vb = (size_t)c->A * c->K * c->N * 8 * sizeof(float);
+    const size_t zb = (size_t)c->I * c->K * c->M * c->N * 8 * sizeof(double);
+    int rc;
+    if ((rc = copy_out(c, J, c->J, vb, ptr_kind))) return rc;
+    if ((rc = copy_out(c, Zo, c->Z, zb, ptr_kind))) return rc;
+    if ((rc = copy_out(c, Yo, c->Y, vb, ptr_kind))) return rc;
+    if (ptr_kind == 0) CK(cudaStreamSynchronize(c->stream));
+    return CALIB_OK;
+}
+
+int calib_get_agent_objective(calib_ctx* c, double* L, double* g) {
+    if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
+    std::vector<AgentState> s(c->A);
+    CK(cudaStreamSynchronize(c->stream));
+    CK(cudaMemcpy(s.data(), c->st, s.size() * sizeof(AgentState), cudaMemcpyDeviceToHost));
+    for (int a = 0; a < c->A; ++a) {
+        if (L) L[a] = s[a].L;
+        if (g) g[a] = s[a].g;
+    }
+    return CALIB_OK;
+}
+
+int calib_eval(calib_ctx* c, const void* Jin, double* L, double* g, void* grad, int ptr_kind) {
+    if (!c || !Jin) return fail(CALIB_EINVAL, "ctx and J are required");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "set visibilities and coherencies first");
+    const size_t vb = (size_t)c->A * c->K * c->N * 8 * sizeof(float);
+    CK(cudaMemcpyAsync(c->evJ, Jin, vb, ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    CK(launch_sweep(sweep_args(c, SWEEP_RESIDUAL, c->evJ, nullptr), SWEEP_RESIDUAL, c->stream));
+    LMArgs la = lm_args(c);
+    la.Jt = c->evJ;
+    CK(launch_eval_output(la, c->evOut, c->evL, c->evG, c->stream));
+    c->launches += 2;
+    int rc;
+    if (grad && (rc = copy_out(c, grad, c->evOut, vb, ptr_kind))) return rc;
+    if (L && (rc = copy_out(c, L, c->evL, (size_t)c->A * sizeof(double), ptr_kind))) return rc;
+    if (g && (rc = copy_out(c, g, c->evG, (size_t)c->A * sizeof(double), ptr_kind))) return rc;
+    if (ptr_kind == 0) {
+        CK(cudaStreamSynchronize(c->stream));
+        return check_status(c);
+    }
+    return CALIB_OK;
+}
+
+int calib_hessvec(calib_ctx* c, const void* Jin, const void* eta, void* out, int ptr_kind) {
+    if (!c || !Jin || !eta || !out) return fail(CALIB_EINVAL, "ctx, J, eta and out are required");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    if (!c->coh_set) return fail(CALIB_ESTATE, "set coherencies first");
+    const size_t vb = (size_t)c->A * c->K * c->N * 8 * sizeof(float);
+    const cudaMemcpyKind kind = ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    CK(cudaMemcpyAsync(c->evJ, Jin, vb, kind, c->stream));
+    CK(cudaMemcpyAsync(c->evE, eta, vb, kind, c->stream));
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    CK(launch_sweep(sweep_args(c, SWEEP_HESSVEC, c->evJ, c->evE), SWEEP_HESSVEC, c->stream));
+    LMArgs la = lm_args(c);
+    la.p = c->evE;
+    CK(launch_hv_output(la, c->evOut, c->stream));
+    c->launches += 2;
+    int rc = copy_out(c, out, c->evOut, vb, ptr_kind);
+    if (rc) return rc;
+    if (ptr_kind == 0) {
+        CK(cudaStreamSynchronize(c->stream));
+        return check_status(c);
+    }
+    return CALIB_OK;
+}
+
+int calib_sync(calib_ctx* c) {
+    if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
+    CK(cudaStreamSynchronize(c->stream));
+    return check_status(c);
+}
+
+int calib_profile_enable(calib_ctx* c, int on) {
+    if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
+    c->profiling = on != 0;
+    c->prof_ms[0] = c->prof_ms[1] = 0.0;
+    c->prof_n[0] = c->prof_n[1] = 0;
+    return CALIB_OK;
+}
+
+int calib_profile_read(calib_ctx* c, int cap, const char** names, double* total_ms, long long* launches,
+                       double* bytes_per_launch) {
+    if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
+    static const char* kNames[2] = {"sweep_residual", "sweep_hessvec"};
+    const double bytes[2] = {c->alg_bytes_res, c->alg_bytes_hv};
+    for (int i = 0; i < 2 && i < cap; ++i) {
+        if (names) names[i] = kNames[i];
+        if (total_ms) total_ms[i] = c->prof_ms[i];
+        if (launches) launches[i] = c->prof_n[i];
+        if (bytes_per_launch) bytes_per_launch[i] = bytes[i];
+    }
+    return 2;
+}
+
+long long calib_launch_count(calib_ctx* c) { return c ? c->launches : 0; }
+
+const char* calib_last_error(void) { return g_err.c_str(); }
+
+void calib_destroy(calib_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    clear_graphs(c);
+    free_layout(c);
+    for (void* p : {(void*)c->J, (void*)c->Jt, (void*)c->Y, (void*)c->BZ, (void*)c->gradg, (void*)c->grad,
+                    (void*)c->x, (void*)c->r, (void*)c->z, (void*)c->p, (void*)c->Ap, (void*)c->Gm,
+                    (void*)c->evJ, (void*)c->evE, (void*)c->evOut, (void*)c->part, (void*)c->part_cost, (void*)c->part_dcost,
+                    (void*)c->Z, (void*)c->Zprev, (void*)c->basis_d, (void*)c->Pinv_d, (void*)c->freqs_d,
+                    (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->stats, (void*)c->iter_counter,
+                    (void*)c->status, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
+                    (void*)c->coh_off_d, c->staging})
+        if (p) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

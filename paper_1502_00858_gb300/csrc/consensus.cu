@@ -1,0 +1,250 @@
+// Fusion-centre and dual steps of C-ADMM (Section 3): first-iteration gauge projection,
+// the closed-form Z-update (Eq. Zest), the dual update (Eq. M3) and the per-iteration
+// residuals of Section 4. On one GPU the paper's agent -> fusion centre -> agent messages
+// become a device reduction over the P agents of each solution interval, ordered by the stream.
+#include <math.h>
+
+#include "calib_internal.cuh"
+
+namespace calib {
+namespace {
+
+constexpr int CT = 256;
+
+__device__ double bsum(double v, double* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+struct C2 { double r, i; };
+__device__ __forceinline__ C2 cm(C2 a, C2 b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ C2 cconj(C2 a) { return {a.r, -a.i}; }
+__device__ __forceinline__ C2 cadd(C2 a, C2 b) { return {a.r + b.r, a.i + b.i}; }
+
+// First C-ADMM iteration (Section 3, initialisation): rotate each agent's J_k by the unitary
+// polar factor U of M = J_k^H J_ref,k (the 2x2 Procrustes solution, min_U ||J_ref - J U||), the
+// reference being the agent at frequency index P/2 of the same interval. For 2x2 M with
+// det M = |det M| e^{i theta}: U = (M + e^{i theta} adj(M)^H) / sqrt(||M||_F^2 + 2 |det M|).
+// The stored data gradient and Jacobi blocks are rotated with J (grad g(JU) = grad g(J) U,
+// G(JU) = U^H G U) since g is invariant under the common unitary.
+__global__ void __launch_bounds__(CT) k_gauge(const ConsArgs a) {
+    __shared__ double red[33];
+    __shared__ C2 U[4];
+    const int agent = blockIdx.x;
+    const int iv = agent / a.P, f = agent - iv * a.P;
+    const int ref = iv * a.P + a.P / 2;
+    if (agent == ref) return;
+    const int N = a.N;
+    for (int k = 0; k < a.K; ++k) {
+        const float* Ja = a.J + ((size_t)agent * a.K + k) * N * 8;
+        const float* Jr = a.J + ((size_t)ref * a.K + k) * N * 8;
+        C2 m[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        for (int p = threadIdx.x; p < N; p += blockDim.x) {
+            C2 ja[4], jr[4];
+            for (int i = 0; i < 4; ++i) {
+                ja[i] = {Ja[p * 8 + 2 * i], Ja[p * 8 + 2 * i + 1]};
+                jr[i] = {Jr[p * 8 + 2 * i], Jr[p * 8 + 2 * i + 1]};
+            }
+            // M[i][j] += sum_m conj(Ja[m][i]) Jr[m][j]
+            for (int i = 0; i < 2; ++i)
+                for (int j = 0; j < 2; ++j)
+                    for (int mm = 0; mm < 2; ++mm) m[i * 2 + j] = cadd(m[i * 2 + j], cm(cconj(ja[mm * 2 + i]), jr[mm * 2 + j]));
+        }
+        double tot[8];
+        for (int i = 0; i < 4; ++i) {
+            tot[2 * i] = bsum(m[i].r, red);
+            tot[2 * i + 1] = bsum(m[i].i, red);
+        }
+        if (threadIdx.x == 0) {
+            const C2 M00 = {tot[0], tot[1]}, M01 = {tot[2], tot[3]}, M10 = {tot[4], tot[5]}, M11 = {tot[6], tot[7]};
+            const C2 det = cadd(cm(M00, M11), {-(cm(M01, M10).r), -(cm(M01, M10).i)});
+            const double adet = hypot(det.r, det.i);
+            const C2 ph = adet > 0 ? C2{det.r / adet, det.i / adet} : C2{1.0, 0.0};
+            // adj(M) = [[M11, -M01], [-M10, M00]]; adj(M)^H = [[conj M11, -conj M10], [-conj M01, conj M00]]
+            const C2 A00 = cconj(M11), A01 = {-M10.r, M10.i}, A10 = {-M01.r, M01.i}, A11 = cconj(M00);
+            const double fro = M00.r * M00.r + M00.i * M00.i + M01.r * M01.r + M01.i * M01.i +
+                               M10.r * M10.r + M10.i * M10.i + M11.r * M11.r + M11.i * M11.i;
+            const double s = sqrt(fro + 2.0 * adet);
+            const double is = s > 0 ? 1.0 / s : 0.0;
+            const C2 u00 = cadd(M00, cm(ph, A00)), u01 = cadd(M01, cm(ph, A01));
+            const C2 u10 = cadd(M10, cm(ph, A10)), u11 = cadd(M11, cm(ph, A11));
+            U[0] = {u00.r * is, u00.i * is};
+            U[1] = {u01.r * is, u01.i * is};
+            U[2] = {u10.r * is, u10.i * is};
+            U[3] = {u11.r * is, u11.i * is};
+            if (!(s > 0)) { U[0] = {1, 0}; U[1] = {0, 0}; U[2] = {0, 0}; U[3] = {1, 0}; }
+        }
+        __syncthreads();
+        float* Jw = a.J + ((size_t)agent * a.K + k) * N * 8;
+        float* Gw = a.gradg + ((size_t)agent * a.K + k) * N * 8;
+        float* Hw = a.Gm + ((size_t)agent * a.K + k) * N * 4;
+        for (int p = threadIdx.x; p < N; p += blockDim.x) {
+            for (int which = 0; which < 2; ++which) {
+                float* X = (which == 0 ? Jw : Gw) + p * 8;
+                C2 x[4], y[4];
+                for (int i = 0; i < 4; ++i) x[i] = {X[2 * i], X[2 * i + 1]};
+                for (int r = 0; r < 2; ++r)
+                    for (int n = 0; n < 2; ++n) y[r * 2 + n] = cadd(cm(x[r * 2 + 0], U[0 * 2 + n]), cm(x[r * 2 + 1], U[1 * 2 + n]));
+                for (int i = 0; i < 4; ++i) { X[2 * i] = (float)y[i].r; X[2 * i + 1] = (float)y[i].i; }
+            }
+            // G <- U^H G U
+            float* Gp = Hw + p * 4;
+            const C2 G00 = {Gp[0], 0}, G11 = {Gp[1], 0}, G01 = {Gp[2], Gp[3]}, G10 = {Gp[2], -Gp[3]};
+            const C2 Gm_[4] = {G00, G01, G10, G11};
+            C2 T[4], R[4];
+            for (int r = 0; r < 2; ++r)  // T = G U
+                for (int n = 0; n < 2; ++n) T[r * 2 + n] = cadd(cm(Gm_[r * 2 + 0], U[0 * 2 + n]), cm(Gm_[r * 2 + 1], U[1 * 2 + n]));
+            for (int r = 0; r < 2; ++r)  // R = U^H T
+                for (int n = 0; n < 2; ++n) R[r * 2 + n] = cadd(cm(cconj(U[0 * 2 + r]), T[0 * 2 + n]), cm(cconj(U[1 * 2 + r]), T[1 * 2 + n]));
+            Gp[0] = (float)R[0].r; Gp[1] = (float)R[3].r; Gp[2] = (float)R[1].r; Gp[3] = (float)R[1].i;
+        }
+        __syncthreads();
+    }
+    (void)f;
+}
+
+// Z_k = (1/rho_k) Pinv (sum_f b(f) (Y_fk + rho_k J_fk)) per interval, direction, station and entry
+// (Eq. Zest in the reshaped form z = vec(R P^T) of Section 3). Float64 accumulation.
+__global__ void __launch_bounds__(CT) k_zupdate(const ConsArgs a) {
+    const long long total = (long long)a.I * a.K * a.N * 8;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const int e = (int)(idx % 8);
+    const long long t1 = idx / 8;
+    const int p = (int)(t1 % a.N);
+    const long long t2 = t1 / a.N;
+    const int k = (int)(t2 % a.K);
+    const int iv = (int)(t2 / a.K);
+    const double rk = a.rho[k];
+    double R[MAX_M];
+    for (int l = 0; l < a.M; ++l) R[l] = 0.0;
+    for (int f = 0; f < a.P; ++f) {
+        const size_t o = (((size_t)(iv * a.P + f) * a.K + k) * a.N + p) * 8 + e;
+        const double v = (double)a.Y[o] + rk * (double)a.J[o];
+        for (int l = 0; l < a.M; ++l) R[l] += a.basis[f * a.M + l] * v;
+    }
+    for (int l = 0; l < a.M; ++l) {
+        double z = 0.0;
+        for (int m = 0; m < a.M; ++m) z += a.Pinv[l * a.M + m] * R[m];
+        const size_t zo = ((((size_t)iv * a.K + k) * a.M + l) * a.N + p) * 8 + e;
+        a.Zprev[zo] = a.Z[zo];
+        a.Z[zo] = z / rk;
+    }
+}
+
+// BZ_i = sum_l b_l(f_i) Z_l; Y_i += rho (J_i - BZ_i) (Eq. M3); per-agent ||J_ik - BZ_ik|| and
+// L_i(J_i, Z, Y_i) = g_i + Re tr(Y^H D) + rho/2 ||D||^2 with the new Y and BZ (Eq. sumtrace2).
+__global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) {
+    __shared__ double red[33];
+    const int agent = blockIdx.x;
+    const int iv = agent / a.P, f = agent - iv * a.P;
+    const int N = a.N;
+    double pen = 0.0;
+    for (int k = 0; k < a.K; ++k) {
+        const double rk = a.rho[k];
+        double dd = 0.0;
+        for (int p = threadIdx.x; p < N; p += blockDim.x) {
+            const size_t o = (((size_t)agent * a.K + k) * N + p) * 8;
+            for (int e = 0; e < 8; ++e) {
+                double bz = 0.0;
+                for (int l = 0; l < a.M; ++l)
+                    bz += a.basis[f * a.M + l] * a.Z[((((size_t)iv * a.K + k) * a.M + l) * N + p) * 8 + e];
+                const double d = (double)a.J[o + e] - bz;
+                const float ynew = update_y ? (float)((double)a.Y[o + e] + rk * d) : a.Y[o + e];
+                a.Y[o + e] = ynew;
+                a.BZ[o + e] = (float)bz;
+                dd += d * d;
+                pen += (double)ynew * d + 0.5 * rk * d * d;
+            }
+        }
+        dd = bsum(dd, red);
+        if (threadIdx.x == 0 && a.prim) a.prim[(size_t)agent * a.K + k] = sqrt(dd);
+    }
+    pen = bsum(pen, red);
+    if (threadIdx.x == 0) a.st[agent].L = a.st[agent].g + pen;
+}
+
+// Per-iteration record (Section 4): primal, dual, objective, data residual norm.
+__global__ void __launch_bounds__(CT) k_stats(const ConsArgs a) {
+    __shared__ double red[33];
+    double prim = 0.0, dual = 0.0, obj = 0.0, g = 0.0;
+    for (int i = threadIdx.x; i < a.A * a.K; i += blockDim.x) prim += a.prim[i];
+    const int per = a.M * a.N * 8;
+    for (int i = threadIdx.x; i < a.I * a.K; i += blockDim.x) {
+        double s = 0.0;
+        const double* Z = a.Z + (size_t)i * per;
+        const double* Zp = a.Zprev + (size_t)i * per;
+        for (int j = 0; j < per; ++j) {
+            const double d = Z[j] - Zp[j];
+            s += d * d;
+        }
+        dual += sqrt(s);
+    }
+    for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
+        obj += a.st[i].L;
+        g += a.st[i].g;
+    }
+    prim = bsum(prim, red);
+    dual = bsum(dual, red);
+    obj = bsum(obj, red);
+    g = bsum(g, red);
+    if (threadIdx.x == 0) {
+        const int it = *a.iter_counter;
+        if (it < a.max_iters) {
+            double* o = a.stats + (size_t)it * 4;
+            o[0] = prim / sqrt(4.0 * a.N) / ((double)a.A * a.K);
+            o[1] = dual / sqrt(4.0 * a.M * a.N) / ((double)a.I * a.K);
+            o[2] = obj;
+            o[3] = sqrt(g);
+        }
+        *a.iter_counter = it + 1;
+    }
+}
+
+__global__ void k_identity(float* J, long long n_blocks) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_blocks) return;
+    float4* p = reinterpret_cast<float4*>(J + i * 8);
+    p[0] = make_float4(1.f, 0.f, 0.f, 0.f);
+    p[1] = make_float4(0.f, 0.f, 1.f, 0.f);
+}
+
+}  // namespace
+
+cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s) {
+    k_gauge<<<a.A, CT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_zupdate(const ConsArgs& a, cudaStream_t s) {
+    const long long total = (long long)a.I * a.K * a.N * 8;
+    k_zupdate<<<(unsigned)((total + CT - 1) / CT), CT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_yupdate(const ConsArgs& a, cudaStream_t s) {
+    k_yupdate<<<a.A, CT, 0, s>>>(a, 1);
+    return cudaGetLastError();
+}
+cudaError_t launch_bz_only(const ConsArgs& a, cudaStream_t s) {
+    k_yupdate<<<a.A, CT, 0, s>>>(a, 0);
+    return cudaGetLastError();
+}
+cudaError_t launch_stats(const ConsArgs& a, cudaStream_t s) {
+    k_stats<<<1, CT, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_identity(float* J, long long n_blocks, cudaStream_t s) {
+    k_identity<<<(unsigned)((n_blocks + 255) / 256), 256, 0, s>>>(J, n_blocks);
+    return cudaGetLastError();
+}
+
+}  // namespace calib

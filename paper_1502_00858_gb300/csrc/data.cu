@@ -1,0 +1,203 @@
+// Data ingestion and coherency prediction.
+//
+// Ingestion moves user-layout visibilities [A][B][T_a][2][2] and coherencies [A][B][T_a][K] into
+// the circulant-diagonal layout used by the sweeps (see calib_internal.cuh); a pair held reversed
+// gets V^H and conj(c), which is the same measurement seen from the other station (Eq. vispq).
+//
+// Prediction (Eq. coh): c_pq = sum_s I_s(f) exp(i phi_pq,s) with phi = -2 pi (f/c)
+// (u_pq l + v_pq m + w_pq (n - 1)) and (u,v,w)_pq = (u,v,w)_p - (u,v,w)_q. The phase splits into
+// station phasors E_ps = exp(-2 pi i turns_ps), turns_ps = (f/c)(u_p l + v_p m + w_p (n-1)), so
+// c_pq = sum_s I_s E_ps conj(E_qs). Turns are formed in float64 and reduced to [-1/2, 1/2]
+// before the float32 sincospi, so the phase error does not grow with baseline length.
+#include <math.h>
+
+#include "calib_internal.cuh"
+
+namespace calib {
+namespace {
+
+constexpr double C_LIGHT = 299792458.0;
+
+__global__ void k_ingest(const IngestArgs a) {
+    const int d = blockIdx.x, agent = blockIdx.y;
+    const DiagDesc dsc = a.desc[(size_t)agent * a.D + d];
+    const int Ta = a.T[agent];
+    const int w = a.is_vis ? 4 : a.K;
+    const long long total = (long long)Ta * dsc.n_pad * w;
+    float2* dst = a.dst + (a.is_vis ? dsc.voff : dsc.coff);
+    const float2* src = a.src + a.src_off[agent];
+    for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+        const int e = (int)(i % w);
+        const long long rest = i / w;
+        const int g = (int)(rest % dsc.n_pad);
+        const int t = (int)(rest / dsc.n_pad);
+        float2 v = make_float2(0.f, 0.f);
+        if (g < dsc.n) {
+            const int sl = a.slot[dsc.slot_off + g];
+            const int rev = (sl >> 16) & 1;
+            const long long b = a.slot_b[dsc.slot_off + g];
+            if (a.is_vis) {
+                const int es = rev ? ((e & 1) * 2 + (e >> 1)) : e;  // V^H: element (r,c) <- conj (c,r)
+                v = src[(b * Ta + t) * 4 + es];
+            } else {
+                v = src[(b * Ta + t) * a.K + e];
+            }
+            if (rev) v.y = -v.y;
+        }
+        dst[i] = v;
+    }
+}
+
+__global__ void k_extract_coh(const IngestArgs a, float2* out) {
+    const int d = blockIdx.x, agent = blockIdx.y;
+    const DiagDesc dsc = a.desc[(size_t)agent * a.D + d];
+    const int Ta = a.T[agent];
+    const long long total = (long long)Ta * dsc.n * a.K;
+    const float2* src = a.dst + dsc.coff;
+    float2* o = out + a.src_off[agent];
+    for (long long i = threadIdx.x; i < total; i += blockDim.x) {
+        const int k = (int)(i % a.K);
+        const long long rest = i / a.K;
+        const int g = (int)(rest % dsc.n);
+        const int t = (int)(rest / dsc.n);
+        const int sl = a.slot[dsc.slot_off + g];
+        const long long b = a.slot_b[dsc.slot_off + g];
+        float2 v = src[((long long)t * dsc.n_pad + g) * a.K + k];
+        if ((sl >> 16) & 1) v.y = -v.y;
+        o[(b * Ta + t) * a.K + k] = v;
+    }
+}
+
+// One CTA per (sample, agent); source chunks sized to fit the phasor table in shared memory.
+__global__ void __launch_bounds__(256) k_predict(const PredictArgs a, int s_chunk) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int t = blockIdx.x, agent = blockIdx.y;
+    const int Ta = a.T[agent];
+    if (t >= Ta) return;
+    const int iv = agent / a.P, fi = agent - iv * a.P;
+    const double f = a.freqs[fi];
+    const int N = a.N, K = a.K;
+    float2* E = reinterpret_cast<float2*>(smem);                          // [K][s_chunk][N]
+    float* flux = reinterpret_cast<float*>(E + (size_t)K * s_chunk * N);  // [K][s_chunk]
+    const double* uvw = a.uvw + (((size_t)iv * a.Tmax + t) * N) * 3;
+    const DiagDesc* dsc_agent = a.desc + (size_t)agent * a.D;
+
+    for (int s0 = 0; s0 < a.S; s0 += s_chunk) {
+        const int ns = min(s_chunk, a.S - s0);
+        for (int i = threadIdx.x; i < K * ns; i += blockDim.x) {
+            const int k = i / ns, s = i - k * ns;
+            const double* src = a.sky + ((size_t)k * a.S + s0 + s) * 4;
+            flux[k * s_chunk + s] = (float)(src[2] * pow(f / a.f0, src[3]));
+        }
+        for (int i = threadIdx.x; i < K * ns * N; i += blockDim.x) {
+            const int p = i % N;
+            const int ks = i / N;
+            const int k = ks / ns, s = ks - k * ns;
+            const double* src = a.sky + ((size_t)k * a.S + s0 + s) * 4;
+            const double l = src[0], m = src[1];
+            const double r2 = l * l + m * m;
+            const double nm1 = -r2 / (1.0 + sqrt(1.0 - r2));  // sqrt(1 - l^2 - m^2) - 1, cancellation-free
+            const double turns = (f / C_LIGHT) * (uvw[p * 3 + 0] * l + uvw[p * 3 + 1] * m + uvw[p * 3 + 2] * nm1);
+            const float fr = (float)(turns - rint(turns));
+            float sn, cs;
+            sincospif(2.0f * fr, &sn, &cs);
+            E[((size_t)k * s_chunk + s) * N + p] = make_float2(cs, -sn);  // exp(-2 pi i turns)
+        }
+        __syncthreads();
+        for (int d = 0; d < a.D; ++d) {
+            const DiagDesc dsc = dsc_agent[d];
+            float2* out = a.C + dsc.coff + (size_t)t * dsc.n_pad * K;
+            for (int it = threadIdx.x; it < dsc.n_pad * K; it += blockDim.x) {
+                const int g = it / K, k = it - g * K;
+                float2 c = make_float2(0.f, 0.f);
+                if (g < dsc.n) {
+                    const int sl = a.slot[dsc.slot_off + g];
+                    const int p = sl & 0xff, q = (sl >> 8) & 0xff;
+                    const float2* Ek = E + (size_t)k * s_chunk * N;
+                    const float* fk = flux + k * s_chunk;
+                    for (int s = 0; s < ns; ++s) {
+                        const float2 ep = Ek[s * N + p], eq = Ek[s * N + q];
+                        // I_s E_p conj(E_q)
+                        const float re = ep.x * eq.x + ep.y * eq.y;
+                        const float im = ep.y * eq.x - ep.x * eq.y;
+                        c.x = fmaf(fk[s], re, c.x);
+                        c.y = fmaf(fk[s], im, c.y);
+                    }
+                }
+                if (s0 == 0) {
+                    out[it] = c;
+                } else {
+                    const float2 o = out[it];
+                    out[it] = make_float2(o.x + c.x, o.y + c.y);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// s_bk = sum_t |c_btk|^2 per slot and direction (fixed for the whole calibration).
+__global__ void k_coh_power(const float2* C, const DiagDesc* desc, const int* T, float* spow, int D, int K) {
+    const int agent = blockIdx.x;
+    const int Ta = T[agent];
+    for (int d = 0; d < D; ++d) {
+        const DiagDesc dsc = desc[(size_t)agent * D + d];
+        for (int it = threadIdx.x; it < dsc.n * K; it += blockDim.x) {
+            const int g = it / K, k = it - g * K;
+            float s = 0.f;
+            for (int t = 0; t < Ta; ++t) {
+                const float2 c = C[dsc.coff + ((size_t)t * dsc.n_pad + g) * K + k];
+                s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
+            }
+            spow[((size_t)dsc.slot_off + g) * K + k] = s;
+        }
+    }
+}
+
+__global__ void k_check_finite(const float* x, long long n, int* status) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    int bad = 0;
+    for (; i < n; i += stride) bad |= !isfinite(x[i]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(status, 2);
+}
+
+}  // namespace
+
+cudaError_t prepare_data_kernels() {
+    return cudaFuncSetAttribute(k_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+}
+
+cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t s) {
+    dim3 grid(a.D, a.A);
+    k_ingest<<<grid, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_extract_coh(const IngestArgs& a, float2* user_dst, cudaStream_t s) {
+    dim3 grid(a.D, a.A);
+    k_extract_coh<<<grid, 256, 0, s>>>(a, user_dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s) {
+    const size_t budget = 96 * 1024;
+    int s_chunk = a.S;
+    while (s_chunk > 1 && (size_t)a.K * s_chunk * (a.N * 8 + 4) > budget) s_chunk = (s_chunk + 1) / 2;
+    const size_t smem = (size_t)a.K * s_chunk * (a.N * 8 + 4);
+    dim3 grid(a.Tmax, a.A);
+    k_predict<<<grid, 256, smem, s>>>(a, s_chunk);
+    return cudaGetLastError();
+}
+cudaError_t launch_coh_power(const float2* C, const DiagDesc* desc, const int* T, float* spow,
+                             int A, int D, int K, cudaStream_t s) {
+    k_coh_power<<<A, 256, 0, s>>>(C, desc, T, spow, D, K);
+    return cudaGetLastError();
+}
+cudaError_t launch_check_finite(const float* x, long long n, int* status, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    k_check_finite<<<(unsigned)blocks, 256, 0, s>>>(x, n, status);
+    return cudaGetLastError();
+}
+
+}  // namespace calib

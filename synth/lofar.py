@@ -292,3 +292,11 @@ def agent_slices(T: np.ndarray, B: int) -> np.ndarray:
 def pack_uniform(arrs: list[np.ndarray], dtype=np.complex64) -> np.ndarray:
     """Concatenate per-agent blocks (agent-major) into one contiguous array."""
     return np.ascontiguousarray(np.concatenate([a.reshape(-1) for a in arrs]).astype(dtype))
+
+
+def user_layout(prob: dict) -> dict:
+    """The problem's arrays in the C-ABI input layout (complex64, agent-major packed):
+    vis [A][B][T_a][2][2], coh [A][B][T_a][K], flags [A][B], plus T [A]."""
+    vis = np.concatenate([V.reshape(-1) for V in prob["V"]]).astype(np.complex64)
+    coh = np.concatenate([C.reshape(-1) for C in prob["C"]]).astype(np.complex64)
+    return dict(vis=vis, coh=coh, flags=np.ascontiguousarray(prob["flags"]), T=prob["T"].astype(np.int32))

@@ -1,0 +1,202 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Tolerances: the hot path computes in float32 with float64 cost, dot products and
+consensus (Z) accumulation, so single-pass quantities are compared at 2e-5..1e-4 of
+their scale, and whole C-ADMM runs at 1e-4 relative on the consensus objective and
+the data residual norm (the parity bar for the iteration).
+
+The dual residual ||Z^{n+1} - Z^n|| is dominated by the slow drift of the common unitary
+gauge of each direction: the data term is exactly flat along it (C = c I_2, Eq. coh) and
+only the penalty curves it, with Hessian rho/2 against ~sum_t |c|^2 |J|^2 for the data.
+Float32 residuals carry an error ~eps |V| per element, so the gauge component of the
+gradient is known to ~eps |V| |J| sum(T) / (rho/2 |dJ_gauge|), a few per cent on these
+inputs; the dual is compared at 15 % relative, with an absolute floor of 1e-5 of the
+solution scale ||Z^1|| / sqrt(4MN) (the first record) where the iteration has converged
+and float32 stops resolving the difference of consecutive Z. With one LM step per
+J-update the gauge mode is not resolved on either side and all four records agree at 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import admm as O
+from paper_1502_00858_gb300 import Calibrator
+from synth import make_problem, user_layout
+
+pytestmark = pytest.mark.gpu
+
+REL_ADMM = 1e-4
+
+
+def cn(rng, *shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / math.sqrt(2)
+
+
+def c64(x):
+    return np.asarray(x).astype(np.complex64).astype(np.complex128)
+
+
+def rounded(prob):
+    """The problem with V and C rounded to complex64, as the GPU sees them."""
+    return dict(prob, V=[c64(v) for v in prob["V"]], C=[c64(c) for c in prob["C"]])
+
+
+def calibrator(lib, prob, **kw):
+    cal = Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
+                     n_intervals=prob["I"], samples=prob["T"], **kw)
+    ul = user_layout(prob)
+    cal.set_data(ul["vis"], ul["coh"], ul["flags"] if ul["flags"].any() else None)
+    return cal
+
+
+def ragged_problem(seed=5):
+    """Odd N, three directions, two intervals, uneven sample counts and flagged baselines."""
+    return make_problem("adjoint_n16_k3", seed=seed, N=13, K=3, P=5, I=2, T=(3, 5, 7), flag_max=0.25)
+
+
+CASES = {
+    "tiny_n8_k1": lambda: make_problem("tiny_n8_k1"),
+    "ragged_n13_k3": ragged_problem,
+    "n2_single_baseline": lambda: make_problem("tiny_n8_k1", N=2, P=3, seed=7),
+    "n3_k2": lambda: make_problem("adjoint_n16_k3", N=3, K=2, P=4, I=1, T=1, seed=8),
+}
+
+
+def random_state(prob, seed):
+    rng = np.random.default_rng(seed)
+    A, K, N, M, I = prob["A"], prob["K"], prob["N"], prob["M"], prob["I"]
+    J = (prob["J_true"] + 0.05 * cn(rng, A, K, N, 2, 2)).astype(np.complex64)
+    Z = 0.1 * cn(rng, I, K, M, N, 2, 2)
+    Y = (0.3 * cn(rng, A, K, N, 2, 2)).astype(np.complex64)
+    return J, Z, Y
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_eval_matches_oracle(lib, case):
+    prob = CASES[case]()
+    pr = rounded(prob)
+    cal = calibrator(lib, prob)
+    J, Z, Y = random_state(prob, 11)
+    cal.set_consensus(Z, Y)
+    L, g, grad = cal.eval(J)
+    P = prob["P"]
+    for a in range(prob["A"]):
+        V, C, pq = O.agent_data(pr, a)
+        BZ = c64(O.bz(Z[a // P], prob["basis"][a % P]))
+        Ja, Ya = J[a].astype(np.complex128), Y[a].astype(np.complex128)
+        go = O.data_cost(Ja, V, C, pq)
+        Lo = O.aug_lagrangian(Ja, V, C, pq, Ya, BZ, prob["rho"])
+        gro = O.grad_lagrangian(Ja, V, C, pq, Ya, BZ, prob["rho"])
+        assert g[a] == pytest.approx(go, rel=2e-5, abs=1e-6)
+        assert L[a] == pytest.approx(Lo, rel=2e-5, abs=1e-6)
+        scale = np.abs(gro).max()
+        assert np.abs(grad[a] - gro).max() <= 1e-4 * scale + 1e-6
+
+
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_hessvec_matches_oracle(lib, case):
+    prob = CASES[case]()
+    pr = rounded(prob)
+    cal = calibrator(lib, prob)
+    J, _, _ = random_state(prob, 12)
+    rng = np.random.default_rng(13)
+    eta = cn(rng, *J.shape).astype(np.complex64)
+    Hv = cal.hessvec(J, eta)
+    for a in range(prob["A"]):
+        V, C, pq = O.agent_data(pr, a)
+        ref = O.hess_lagrangian(J[a].astype(np.complex128), eta[a].astype(np.complex128), C, pq, prob["rho"])
+        assert np.abs(Hv[a] - ref).max() <= 1e-4 * np.abs(ref).max() + 1e-6
+
+
+def test_eval_is_bitwise_reproducible(lib):
+    prob = ragged_problem()
+    cal = calibrator(lib, prob)
+    J, Z, Y = random_state(prob, 14)
+    cal.set_consensus(Z, Y)
+    r1 = cal.eval(J)
+    r2 = cal.eval(J)
+    for x, y in zip(r1, r2):
+        assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("case", ["tiny_n8_k1", "ragged_n13_k3"])
+def test_predict_matches_oracle(lib, case):
+    prob = CASES[case]()
+    cal = calibrator(lib, prob)
+    cal.predict(prob["uvw"], prob["sky"], prob["f0"])
+    got = cal.coherencies()
+    off = 0
+    P, B, K = prob["P"], prob["B"], prob["K"]
+    for a in range(prob["A"]):
+        iv, f = divmod(a, P)
+        Ta = int(prob["T"][a])
+        blk = got[off: off + B * Ta * K].reshape(B, Ta, K)
+        off += B * Ta * K
+        ref = O.predict_coherencies(prob["uvw"][iv, :Ta], prob["sky"], prob["freqs"][f], prob["f0"], prob["pq"])
+        flux = (prob["sky"][..., 2] * (prob["freqs"][f] / prob["f0"]) ** prob["sky"][..., 3]).sum(-1)
+        keep = prob["flags"][a] == 0
+        err = np.abs(blk[keep] - ref[keep]).max(axis=(0, 1))
+        assert np.all(err <= 2e-5 * flux), (a, err / flux)
+        assert np.all(blk[~keep] == 0)
+
+
+def run_both(lib, prob, n_iter, n_lm=10, n_cg=4):
+    cal = calibrator(lib, prob, n_lm=n_lm, n_cg=n_cg)
+    hist = cal.iterate(n_iter)
+    ref = O.admm(rounded(prob), n_iter, n_lm=n_lm, n_cg=n_cg)["hist"]
+    return cal, hist, ref
+
+
+@pytest.mark.parametrize("case", ["tiny_n8_k1", "ragged_n13_k3", "n2_single_baseline"])
+def test_admm_history_matches_oracle(lib, case):
+    prob = CASES[case]()
+    n_iter = 10 if case == "tiny_n8_k1" else 4
+    _, hist, ref = run_both(lib, prob, n_iter)
+    np.testing.assert_allclose(hist["objective"], ref["objective"], rtol=REL_ADMM)
+    np.testing.assert_allclose(hist["resid_norm"], ref["resid_norm"], rtol=REL_ADMM)
+    np.testing.assert_allclose(hist["primal"], ref["primal"], rtol=1e-3, atol=1e-7)
+    np.testing.assert_allclose(hist["dual"], ref["dual"], rtol=0.15, atol=1e-5 * ref["dual"][0])
+
+
+@pytest.mark.parametrize("case,n_cg", [("n3_k2", 1), ("tiny_n8_k1", 4), ("ragged_n13_k3", 4)])
+def test_admm_one_lm_step_matches_all_records(lib, case, n_cg):
+    """n_lm = 1 (and n_cg = 1: one preconditioned steepest-descent step): the gauge mode is
+    not resolved, so primal and dual residuals agree at 1e-4 as well."""
+    prob = CASES[case]()
+    _, hist, ref = run_both(lib, prob, 3, n_lm=1, n_cg=n_cg)
+    for key in ("objective", "resid_norm", "primal", "dual"):
+        np.testing.assert_allclose(hist[key], ref[key], rtol=REL_ADMM, atol=1e-9, err_msg=key)
+
+
+def test_admm_solutions_match_oracle_after_gauge(lib):
+    """J after 5 iterations agrees with the oracle's up to float32 round-off; the gauge is
+    fixed by the first-iteration projection and Z, so no Procrustes is needed here."""
+    prob = CASES["tiny_n8_k1"]()
+    cal = calibrator(lib, prob)
+    cal.iterate(5)
+    J, Z, Y = cal.solutions()
+    ref = O.admm(rounded(prob), 5)
+    for a in range(prob["A"]):
+        assert np.abs(J[a] - ref["J"][a]).max() < 2e-3
+    assert np.abs(Z[0] - ref["Z"][0]).max() < 2e-3
+
+
+def test_full_size_lofar_interval_sample(lib):
+    """The full LOFAR-shaped batch (62 stations, 5 directions, 32 subbands, 10 intervals,
+    10 samples) in the benchmark's launch configuration; the oracle recomputes interval 0."""
+    prob = make_problem("lofar_n62_k5")
+    n_iter = 2
+    cal = calibrator(lib, prob)
+    hist = cal.iterate(n_iter)
+    L, g = cal.agent_objective()
+    ref = O.admm(rounded(prob), n_iter, intervals=[0])
+    P = prob["P"]
+    assert float(np.sum(L[:P])) == pytest.approx(sum(ref["L"][a] for a in range(P)), rel=REL_ADMM)
+    assert float(np.sum(g[:P])) == pytest.approx(sum(ref["g"][a] for a in range(P)), rel=REL_ADMM)
+    assert np.all(np.isfinite(hist["objective"]))
+    # every interval converges to the noise floor: g ~ noise power x (data - parameters)
+    sig2 = 2 * prob["sigma"] ** 2
+    n_data = prob["B"] * 10 * 4
+    n_par = prob["K"] * prob["N"] * 8 / 2
+    assert np.all(g / (sig2 * (n_data - n_par)) < 1.5)
