@@ -21,7 +21,7 @@ EXPORTED = [
     "calib_default_options", "calib_init", "calib_set_data", "calib_predict", "calib_get_coherencies",
     "calib_reset", "calib_set_initial", "calib_set_consensus", "calib_admm_iter", "calib_get_solutions",
     "calib_get_agent_objective", "calib_eval", "calib_hessvec", "calib_sync", "calib_profile_enable",
-    "calib_profile_read", "calib_launch_count", "calib_last_error", "calib_destroy",
+    "calib_profile_read", "calib_launch_count", "calib_last_error", "calib_destroy", "calib_eval_noalloc",
 ]
 
 
@@ -73,6 +73,7 @@ def load(path: str = LIB_PATH):
         "calib_launch_count": (C.c_longlong, [vp]),
         "calib_last_error": (C.c_char_p, []),
         "calib_destroy": (None, [vp]),
+        "calib_eval_noalloc": (i, [i, i, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -238,3 +239,13 @@ def calib_launch_count(ctx) -> int:
 def calib_destroy(ctx):
     if ctx:
         load().calib_destroy(ctx)
+
+
+def calib_eval_noalloc(n_agents, n_stations, n_baselines, n_dirs, n_samples, pq, vis, coh, J, Y, BZ, rho,
+                       L, g, grad, cuda_stream=None):
+    """Device tensors in, device tensors out; rho is a host array. Allocates nothing."""
+    rh = np.ascontiguousarray(rho, dtype=np.float64)
+    ptrs = [_ptr(x)[0] for x in (pq, vis, coh, J, Y, BZ)]
+    _check(load().calib_eval_noalloc(int(n_agents), int(n_stations), int(n_baselines), int(n_dirs),
+                                     int(n_samples), *ptrs, rh.ctypes.data, _ptr(L)[0], _ptr(g)[0],
+                                     _ptr(grad)[0], cuda_stream))

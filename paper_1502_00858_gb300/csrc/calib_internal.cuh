@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 namespace calib {
 
 constexpr int MAX_N = 256;
@@ -144,5 +146,8 @@ cudaError_t launch_check_finite(const float* x, long long n, int* status, cudaSt
 cudaError_t prepare_sweep_kernels();
 cudaError_t prepare_lm_kernels();
 cudaError_t prepare_data_kernels();
+
+// Record the message returned by calib_last_error() on this thread (capi.cu).
+void set_last_error(const std::string& msg);
 
 }  // namespace calib

@@ -421,6 +421,8 @@ bool valid_kind(int k) { return k == 0 || k == 1; }
 
 }  // namespace
 
+void calib::set_last_error(const std::string& msg) { g_err = msg; }
+
 extern "C" {
 
 void calib_default_options(calib_options* opt) {
