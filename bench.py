@@ -195,6 +195,19 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     capi.calib_set_data(cal.ctx, vis_d)  # device pointers: stream-ordered
 
+    if args.kernels_only:
+        # One launch of each sweep mode on the full workload (for a profiler capture), then exit.
+        capi.calib_predict(cal.ctx, uvw_d, sky_d, prob["f0"])
+        J = np.ascontiguousarray(prob["J_true"], dtype=np.complex64)
+        cal.eval(J)
+        cal.hessvec(J, J)
+        capi.calib_reset(cal.ctx)
+        capi.calib_admm_iter(cal.ctx, 1, want_hist=False)
+        torch.cuda.synchronize()
+        cal.close()
+        print("kernels-only run done", flush=True)
+        return
+
     def step():
         capi.calib_predict(cal.ctx, uvw_d, sky_d, prob["f0"])
         capi.calib_reset(cal.ctx)
@@ -320,6 +333,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--chunk-diagonals", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--kernels-only", action="store_true",
+                    help="run one launch of each sweep on the workload and exit (profiler captures)")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.impl == "reference":

@@ -83,7 +83,7 @@ void calib_default_options(calib_options* opt);
 
 /* Create a context for a fixed problem shape (Section 3 problem statement, Eq. hidden,
  * Eq. poly, Eq. Zest).
- *  n_stations N in [2, 256]; n_baselines B in [1, N(N-1)/2];
+ *  n_stations N in [2, 128]; n_baselines B in [1, N(N-1)/2];
  *  pq        [B][2] int32 station pairs with 0 <= p < q < N, no duplicates (host);
  *  n_dirs    K in [1, 16];   n_freqs P >= 1;   freqs_hz [P] (host; stored for calib_predict);
  *  n_basis   M in [1, 16] with P >= M;  basis [P][M] row-major b_l(f_i) (host, float64);

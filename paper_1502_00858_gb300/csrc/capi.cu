@@ -88,6 +88,7 @@ struct calib_ctx {
     float* rho_d = nullptr;
     AgentState* st = nullptr;
     double* prim = nullptr;
+    double* dual2 = nullptr;
     double* stats = nullptr;
     int max_iters = 0;
     int* iter_counter = nullptr;
@@ -179,6 +180,7 @@ ConsArgs cons_args(calib_ctx* c) {
     a.rho = c->rho_d;
     a.st = c->st;
     a.prim = c->prim;
+    a.dual2 = c->dual2;
     a.stats = c->stats;
     a.iter_counter = c->iter_counter;
     a.A = c->A;
@@ -536,6 +538,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     okm = okm && dalloc(&c->basis_d, (size_t)P * M) == cudaSuccess && dalloc(&c->Pinv_d, (size_t)M * M) == cudaSuccess;
     okm = okm && dalloc(&c->freqs_d, (size_t)P) == cudaSuccess && dalloc(&c->rho_d, (size_t)K) == cudaSuccess;
     okm = okm && dalloc(&c->st, (size_t)A) == cudaSuccess && dalloc(&c->prim, (size_t)A * K) == cudaSuccess;
+    okm = okm && dalloc(&c->dual2, (size_t)c->I * K) == cudaSuccess;
     okm = okm && dalloc(&c->iter_counter, 1) == cudaSuccess && dalloc(&c->status, 1) == cudaSuccess;
     okm = okm && dalloc(&c->evL, (size_t)A) == cudaSuccess && dalloc(&c->evG, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess;
@@ -903,7 +906,7 @@ void calib_destroy(calib_ctx* c) {
                     (void*)c->x, (void*)c->r, (void*)c->z, (void*)c->p, (void*)c->Ap, (void*)c->Gm,
                     (void*)c->evJ, (void*)c->evE, (void*)c->evOut, (void*)c->part, (void*)c->part_cost, (void*)c->part_dcost,
                     (void*)c->Z, (void*)c->Zprev, (void*)c->basis_d, (void*)c->Pinv_d, (void*)c->freqs_d,
-                    (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->stats, (void*)c->iter_counter,
+                    (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->dual2, (void*)c->stats, (void*)c->iter_counter,
                     (void*)c->status, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
                     (void*)c->coh_off_d, c->staging})
         if (p) cudaFree(p);

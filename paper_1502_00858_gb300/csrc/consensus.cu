@@ -114,32 +114,36 @@ __global__ void __launch_bounds__(CT) k_gauge(const ConsArgs a) {
 }
 
 // Z_k = (1/rho_k) Pinv (sum_f b(f) (Y_fk + rho_k J_fk)) per interval, direction, station and entry
-// (Eq. Zest in the reshaped form z = vec(R P^T) of Section 3). Float64 accumulation.
+// (Eq. Zest in the reshaped form z = vec(R P^T) of Section 3). One CTA per (interval, direction);
+// float64 accumulation. Also forms ||Z_k^{n+1} - Z_k^n||^2 for the dual residual (Section 4).
 __global__ void __launch_bounds__(CT) k_zupdate(const ConsArgs a) {
-    const long long total = (long long)a.I * a.K * a.N * 8;
-    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const int e = (int)(idx % 8);
-    const long long t1 = idx / 8;
-    const int p = (int)(t1 % a.N);
-    const long long t2 = t1 / a.N;
-    const int k = (int)(t2 % a.K);
-    const int iv = (int)(t2 / a.K);
+    __shared__ double red[33];
+    const int ivk = blockIdx.x;
+    const int k = ivk % a.K, iv = ivk / a.K;
     const double rk = a.rho[k];
-    double R[MAX_M];
-    for (int l = 0; l < a.M; ++l) R[l] = 0.0;
-    for (int f = 0; f < a.P; ++f) {
-        const size_t o = (((size_t)(iv * a.P + f) * a.K + k) * a.N + p) * 8 + e;
-        const double v = (double)a.Y[o] + rk * (double)a.J[o];
-        for (int l = 0; l < a.M; ++l) R[l] += a.basis[f * a.M + l] * v;
+    double dz2 = 0.0;
+    for (int j = threadIdx.x; j < a.N * 8; j += blockDim.x) {
+        const int p = j / 8, e = j % 8;
+        double R[MAX_M];
+        for (int l = 0; l < a.M; ++l) R[l] = 0.0;
+        for (int f = 0; f < a.P; ++f) {
+            const size_t o = (((size_t)(iv * a.P + f) * a.K + k) * a.N + p) * 8 + e;
+            const double v = (double)a.Y[o] + rk * (double)a.J[o];
+            for (int l = 0; l < a.M; ++l) R[l] += a.basis[f * a.M + l] * v;
+        }
+        for (int l = 0; l < a.M; ++l) {
+            double z = 0.0;
+            for (int m = 0; m < a.M; ++m) z += a.Pinv[l * a.M + m] * R[m];
+            z /= rk;
+            const size_t zo = ((((size_t)iv * a.K + k) * a.M + l) * a.N + p) * 8 + e;
+            const double old = a.Z[zo];
+            a.Zprev[zo] = old;
+            a.Z[zo] = z;
+            dz2 += (z - old) * (z - old);
+        }
     }
-    for (int l = 0; l < a.M; ++l) {
-        double z = 0.0;
-        for (int m = 0; m < a.M; ++m) z += a.Pinv[l * a.M + m] * R[m];
-        const size_t zo = ((((size_t)iv * a.K + k) * a.M + l) * a.N + p) * 8 + e;
-        a.Zprev[zo] = a.Z[zo];
-        a.Z[zo] = z / rk;
-    }
+    dz2 = bsum(dz2, red);
+    if (threadIdx.x == 0) a.dual2[ivk] = dz2;
 }
 
 // BZ_i = sum_l b_l(f_i) Z_l; Y_i += rho (J_i - BZ_i) (Eq. M3); per-agent ||J_ik - BZ_ik|| and
@@ -179,17 +183,7 @@ __global__ void __launch_bounds__(CT) k_stats(const ConsArgs a) {
     __shared__ double red[33];
     double prim = 0.0, dual = 0.0, obj = 0.0, g = 0.0;
     for (int i = threadIdx.x; i < a.A * a.K; i += blockDim.x) prim += a.prim[i];
-    const int per = a.M * a.N * 8;
-    for (int i = threadIdx.x; i < a.I * a.K; i += blockDim.x) {
-        double s = 0.0;
-        const double* Z = a.Z + (size_t)i * per;
-        const double* Zp = a.Zprev + (size_t)i * per;
-        for (int j = 0; j < per; ++j) {
-            const double d = Z[j] - Zp[j];
-            s += d * d;
-        }
-        dual += sqrt(s);
-    }
+    for (int i = threadIdx.x; i < a.I * a.K; i += blockDim.x) dual += sqrt(a.dual2[i]);
     for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
         obj += a.st[i].L;
         g += a.st[i].g;
@@ -226,8 +220,7 @@ cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_zupdate(const ConsArgs& a, cudaStream_t s) {
-    const long long total = (long long)a.I * a.K * a.N * 8;
-    k_zupdate<<<(unsigned)((total + CT - 1) / CT), CT, 0, s>>>(a);
+    k_zupdate<<<a.I * a.K, CT, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_yupdate(const ConsArgs& a, cudaStream_t s) {

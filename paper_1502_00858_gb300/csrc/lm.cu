@@ -70,30 +70,31 @@ __device__ __forceinline__ void store_blk(float* base, int blk, const Blk& b) {
     p[0] = make_float4(b.v[0], b.v[1], b.v[2], b.v[3]);
     p[1] = make_float4(b.v[4], b.v[5], b.v[6], b.v[7]);
 }
-__device__ __forceinline__ double dot_blk(const Blk& a, const Blk& b) {
-    double s = 0.0;
+// Per-block dot products are float32 (8 terms); each thread sums its blocks in float32 and the
+// cross-thread reduction is float64 (float64 arithmetic is scarce on this GPU).
+__device__ __forceinline__ float dot_blk(const Blk& a, const Blk& b) {
+    float s = 0.f;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) s += (double)a.v[i] * (double)b.v[i];
+    for (int i = 0; i < 8; ++i) s = fmaf(a.v[i], b.v[i], s);
     return s;
 }
 
 // x (G + lam I)^-1 for a 2x2 complex block x (row-major re,im pairs) and Hermitian G (g00, g11, re g01, im g01).
-__device__ __forceinline__ Blk precond(const Blk& x, const float* G, double lam) {
-    const double a = (double)G[0] + lam, c = (double)G[1] + lam, br = G[2], bi = G[3];
-    const double det = a * c - (br * br + bi * bi);
-    const double id = 1.0 / det;
-    // Minv = id * [[c, -b], [-conj(b), a]]
-    const double m00r = c * id, m00i = 0.0, m01r = -br * id, m01i = -bi * id;
-    const double m10r = -br * id, m10i = bi * id, m11r = a * id, m11i = 0.0;
+__device__ __forceinline__ Blk precond(const Blk& x, const float* G, float lam) {
+    const float a = G[0] + lam, c = G[1] + lam, br = G[2], bi = G[3];
+    const float id = 1.f / (a * c - (br * br + bi * bi));
+    // Minv = id * [[c, -b], [-conj(b), a]]  (m00, m11 real)
+    const float m00 = c * id, m01r = -br * id, m01i = -bi * id;
+    const float m10r = -br * id, m10i = bi * id, m11 = a * id;
     Blk z;
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
-        const double x0r = x.v[r * 4 + 0], x0i = x.v[r * 4 + 1], x1r = x.v[r * 4 + 2], x1i = x.v[r * 4 + 3];
+        const float x0r = x.v[r * 4 + 0], x0i = x.v[r * 4 + 1], x1r = x.v[r * 4 + 2], x1i = x.v[r * 4 + 3];
         // z[r][0] = x[r][0] m00 + x[r][1] m10 ; z[r][1] = x[r][0] m01 + x[r][1] m11
-        z.v[r * 4 + 0] = (float)(x0r * m00r - x0i * m00i + x1r * m10r - x1i * m10i);
-        z.v[r * 4 + 1] = (float)(x0r * m00i + x0i * m00r + x1r * m10i + x1i * m10r);
-        z.v[r * 4 + 2] = (float)(x0r * m01r - x0i * m01i + x1r * m11r - x1i * m11i);
-        z.v[r * 4 + 3] = (float)(x0r * m01i + x0i * m01r + x1r * m11i + x1i * m11r);
+        z.v[r * 4 + 0] = x0r * m00 + x1r * m10r - x1i * m10i;
+        z.v[r * 4 + 1] = x0i * m00 + x1r * m10i + x1i * m10r;
+        z.v[r * 4 + 2] = x0r * m01r - x0i * m01i + x1r * m11;
+        z.v[r * 4 + 3] = x0r * m01i + x0i * m01r + x1i * m11;
     }
     return z;
 }
@@ -114,38 +115,139 @@ __device__ __forceinline__ Blk sum_parts(const LMArgs& a, int agent, int blk, in
 // Penalty Re tr(Y^H D) + rho/2 ||D||^2, D = J - BZ (Eq. sumtrace2), this thread's share.
 __device__ double penalty_part(const float* J, const float* Y, const float* BZ, const float* rho,
                                int N, int KN) {
-    double pen = 0.0;
+    float pen = 0.f;
     for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) {
         const int k = blk / N;
         const Blk j = load_blk(J, blk), y = load_blk(Y, blk), bz = load_blk(BZ, blk);
-        double yd = 0.0, dd = 0.0;
+        float yd = 0.f, dd = 0.f;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const double d = (double)j.v[i] - (double)bz.v[i];
-            yd += (double)y.v[i] * d;
-            dd += d * d;
+            const float d = j.v[i] - bz.v[i];
+            yd = fmaf(y.v[i], d, yd);
+            dd = fmaf(d, d, dd);
         }
-        pen += yd + 0.5 * (double)rho[k] * dd;
+        pen += yd + 0.5f * rho[k] * dd;
     }
-    return pen;
+    return (double)pen;
 }
 
 // Decrease of the penalty from J to Jt, pen(J) - pen(Jt) = -(Re tr(Y^H x) + rho Re tr(D^H x) + rho/2 ||x||^2)
-// with D = J - BZ and x = Jt - J (exact in float64 for float32 operands), this thread's share.
+// with D = J - BZ and x = Jt - J, this thread's share. Formed from the small x, so it is accurate
+// relative to the decrease itself.
 __device__ double penalty_decrease_part(const float* J, const float* Jt, const float* Y, const float* BZ,
                                         const float* rho, int N, int KN) {
-    double s = 0.0;
+    float s = 0.f;
     for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) {
-        const double rk = rho[blk / N];
+        const float rk = rho[blk / N];
         const Blk j = load_blk(J, blk), jt = load_blk(Jt, blk), y = load_blk(Y, blk), bz = load_blk(BZ, blk);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            const double x = (double)jt.v[i] - (double)j.v[i];
-            const double d = (double)j.v[i] - (double)bz.v[i];
-            s -= (double)y.v[i] * x + rk * d * x + 0.5 * rk * x * x;
+            const float x = jt.v[i] - j.v[i];  // exact: Jt = J + x was rounded once
+            const float d = j.v[i] - bz.v[i];
+            s -= fmaf(y.v[i], x, rk * fmaf(0.5f * x, x, d * x));
         }
     }
-    return s;
+    return (double)s;
+}
+
+// Sum of NV values over the CTA (float64, fixed order); results in out[0..NV).
+template <int NV>
+__device__ void block_sum_vec(double (&v)[NV], double* red, double* out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i)
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], o);
+    __syncthreads();
+    if (lane == 0)
+        for (int i = 0; i < NV; ++i) red[w * NV + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int j = 0; j < nw; ++j) s += red[j * NV + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+}
+
+// Remove the component of a data gradient G_k along the gauge orbit {J_k A : A anti-Hermitian}.
+// g is invariant under J_k -> J_k U (C = c I_2, Eq. coh), so its exact gradient has none: the
+// anti-Hermitian part of J_k^H G_k vanishes. Float32 residuals leave round-off there, which would
+// otherwise steer the weakly determined gauge mode (curved only by the rho/2 penalty). With
+// S = J^H J, solve (S A + A S)/2 = skew(J^H G) for A = [[i a, b + i c], [-b + i c, i d]] and set
+// G <- G - J A (the h-orthogonal projection). Exact arithmetic leaves G unchanged.
+__device__ void project_out_gauge(const float* J, float* G, int N, int K, double* red, double* sh) {
+    for (int k = 0; k < K; ++k) {
+        const float* Jk = J + (size_t)k * N * 8;
+        float* Gk = G + (size_t)k * N * 8;
+        double v[12] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+        for (int p = threadIdx.x; p < N; p += blockDim.x) {
+            const float* j = Jk + p * 8;
+            const float* g = Gk + p * 8;
+            // S += J^H J (s0, s1, re s01, im s01); M += J^H G (4 complex, row-major)
+            for (int m = 0; m < 2; ++m) {
+                const double j0r = j[m * 4 + 0], j0i = j[m * 4 + 1], j1r = j[m * 4 + 2], j1i = j[m * 4 + 3];
+                v[0] += j0r * j0r + j0i * j0i;
+                v[1] += j1r * j1r + j1i * j1i;
+                v[2] += j0r * j1r + j0i * j1i;
+                v[3] += j0r * j1i - j0i * j1r;
+                for (int c = 0; c < 2; ++c) {
+                    const double gr = g[m * 4 + 2 * c], gi = g[m * 4 + 2 * c + 1];
+                    // M[0][c] += conj(J[m][0]) G[m][c]; M[1][c] += conj(J[m][1]) G[m][c]
+                    v[4 + 2 * c] += j0r * gr + j0i * gi;
+                    v[5 + 2 * c] += j0r * gi - j0i * gr;
+                    v[8 + 2 * c] += j1r * gr + j1i * gi;
+                    v[9 + 2 * c] += j1r * gi - j1i * gr;
+                }
+            }
+        }
+        block_sum_vec<12>(v, red, sh);
+        if (threadIdx.x == 0) {
+            const double s0 = sh[0], s1 = sh[1], u = sh[2], w = sh[3];
+            // skew(M): t0 = Im M00, t1 = Im M11, t2 + i t3 = (M01 - conj(M10)) / 2
+            const double t0 = sh[5], t1 = sh[11];
+            const double t2 = 0.5 * (sh[6] - sh[8]), t3 = 0.5 * (sh[7] + sh[9]);
+            // unknowns (a, d, b, c):  a s0 + u c - w b = t0;  d s1 + u c - w b = t1;
+            // (b (s0+s1) - w (a+d)) / 2 = t2;  (c (s0+s1) + u (a+d)) / 2 = t3
+            double Mx[4][5] = {{s0, 0.0, -w, u, t0},
+                               {0.0, s1, -w, u, t1},
+                               {-0.5 * w, -0.5 * w, 0.5 * (s0 + s1), 0.0, t2},
+                               {0.5 * u, 0.5 * u, 0.0, 0.5 * (s0 + s1), t3}};
+            bool ok = true;
+            for (int col = 0; col < 4 && ok; ++col) {
+                int piv = col;
+                for (int r = col + 1; r < 4; ++r)
+                    if (fabs(Mx[r][col]) > fabs(Mx[piv][col])) piv = r;
+                if (!(fabs(Mx[piv][col]) > 1e-30)) { ok = false; break; }
+                for (int cc = 0; cc < 5; ++cc) { const double tmp = Mx[col][cc]; Mx[col][cc] = Mx[piv][cc]; Mx[piv][cc] = tmp; }
+                for (int r = 0; r < 4; ++r) {
+                    if (r == col) continue;
+                    const double f = Mx[r][col] / Mx[col][col];
+                    for (int cc = col; cc < 5; ++cc) Mx[r][cc] -= f * Mx[col][cc];
+                }
+            }
+            sh[12] = ok ? Mx[0][4] / Mx[0][0] : 0.0;  // a
+            sh[13] = ok ? Mx[1][4] / Mx[1][1] : 0.0;  // d
+            sh[14] = ok ? Mx[2][4] / Mx[2][2] : 0.0;  // b
+            sh[15] = ok ? Mx[3][4] / Mx[3][3] : 0.0;  // c
+        }
+        __syncthreads();
+        const float a = (float)sh[12], d = (float)sh[13], b = (float)sh[14], c = (float)sh[15];
+        // A = [[i a, b + i c], [-b + i c, i d]]
+        const float A00r = 0.f, A00i = a, A01r = b, A01i = c, A10r = -b, A10i = c, A11r = 0.f, A11i = d;
+        for (int p = threadIdx.x; p < N; p += blockDim.x) {
+            const float* j = Jk + p * 8;
+            float* g = Gk + p * 8;
+            for (int r = 0; r < 2; ++r) {
+                const float jr0 = j[r * 4 + 0], ji0 = j[r * 4 + 1], jr1 = j[r * 4 + 2], ji1 = j[r * 4 + 3];
+                // (J A)[r][0] = J[r][0] A00 + J[r][1] A10 ; (J A)[r][1] = J[r][0] A01 + J[r][1] A11
+                g[r * 4 + 0] -= jr0 * A00r - ji0 * A00i + jr1 * A10r - ji1 * A10i;
+                g[r * 4 + 1] -= jr0 * A00i + ji0 * A00r + jr1 * A10i + ji1 * A10r;
+                g[r * 4 + 2] -= jr0 * A01r - ji0 * A01i + jr1 * A11r - ji1 * A11i;
+                g[r * 4 + 3] -= jr0 * A01i + ji0 * A01r + jr1 * A11i + ji1 * A11r;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // Jacobi blocks G_pk = sum over slots incident on p of s_bk J_ok^H J_ok at the current J, via the
@@ -190,21 +292,21 @@ __device__ void cg_init(const LMArgs& a, int agent, const float* G, double* red)
     const int N = a.N, KN = a.K * N;
     const size_t off = (size_t)agent * KN * 8;
     AgentState& st = a.st[agent];
-    const double mu = st.mu;
-    double rz = 0.0;
+    const float mu = (float)st.mu;
+    float rz = 0.f;
     for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) {
         const int k = blk / N;
-        const double rk = a.rho[k];
+        const float rk = a.rho[k];
         const Blk gg = load_blk(a.gradg + off, blk), y = load_blk(a.Y + off, blk);
         const Blk j = load_blk(a.J + off, blk), bz = load_blk(a.BZ + off, blk);
         Blk gr, r, zero;
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            gr.v[i] = (float)((double)gg.v[i] + 0.5 * (double)y.v[i] + 0.5 * rk * ((double)j.v[i] - (double)bz.v[i]));
+            gr.v[i] = gg.v[i] + 0.5f * y.v[i] + 0.5f * rk * (j.v[i] - bz.v[i]);
             r.v[i] = -gr.v[i];
             zero.v[i] = 0.f;
         }
-        const Blk z = precond(r, G + (size_t)blk * 4, 0.5 * rk + mu);
+        const Blk z = precond(r, G + (size_t)blk * 4, 0.5f * rk + mu);
         store_blk(a.grad + off, blk, gr);
         store_blk(a.r + off, blk, r);
         store_blk(a.z + off, blk, z);
@@ -212,10 +314,10 @@ __device__ void cg_init(const LMArgs& a, int agent, const float* G, double* red)
         store_blk(a.x + off, blk, zero);
         rz += dot_blk(r, z);
     }
-    rz = 2.0 * block_sum(rz, red);
+    const double rzd = 2.0 * block_sum((double)rz, red);
     if (threadIdx.x == 0) {
-        st.rz = rz;
-        st.cg_stop = (rz > 0.0) ? 0 : 1;
+        st.rz = rzd;
+        st.cg_stop = (rzd > 0.0) ? 0 : 1;
     }
 }
 
@@ -229,8 +331,12 @@ __global__ void __launch_bounds__(LM_THREADS) k_lm_eval(const LMArgs a, int mode
     float* Gs = sm + KN * 4;
     AgentState& st = a.st[agent];
 
+    __shared__ double redv[32 * 12];
+    __shared__ double shv[16];
     if (mode == LM_BEGIN_FROM_PARTIALS) {
         for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) store_blk(a.gradg + off, blk, sum_parts(a, agent, blk, KN));
+        __syncthreads();
+        project_out_gauge(a.J + off, a.gradg + off, N, K, redv, shv);
         const double pen = block_sum(penalty_part(a.J + off, a.Y + off, a.BZ + off, a.rho, N, KN), red);
         if (threadIdx.x == 0) {
             double g = 0.0;
@@ -281,6 +387,7 @@ __global__ void __launch_bounds__(LM_THREADS) k_lm_eval(const LMArgs a, int mode
                 store_blk(a.J + off, blk, load_blk(a.Jt + off, blk));
             }
             __syncthreads();
+            project_out_gauge(a.J + off, a.gradg + off, N, K, redv, shv);
             gram_blocks(a, agent, a.J + off, a.Gm + (size_t)agent * KN * 4, Xs, Gs);
         }
     }
@@ -311,49 +418,50 @@ __global__ void __launch_bounds__(LM_THREADS) k_cg_step(const LMArgs a) {
     AgentState& st = a.st[agent];
     const int stop = st.cg_stop;
     if (stop) return;
-    const double mu = st.mu, rz = st.rz;
+    const float mu = (float)st.mu;
+    const double rz = st.rz;
     const float* G = a.Gm + (size_t)agent * KN * 4;
 
-    double pAp = 0.0;
+    float pAp_t = 0.f;
     for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) {
-        const float lam = (float)(0.5 * (double)a.rho[blk / N] + mu);
+        const float lam = 0.5f * a.rho[blk / N] + mu;
         const Blk hp = sum_parts(a, agent, blk, KN);
         const Blk p = load_blk(a.p + off, blk);
         Blk ap;
 #pragma unroll
         for (int i = 0; i < 8; ++i) ap.v[i] = hp.v[i] + lam * p.v[i];
         store_blk(a.Ap + off, blk, ap);
-        pAp += dot_blk(p, ap);
+        pAp_t += dot_blk(p, ap);
     }
-    pAp = 2.0 * block_sum(pAp, red);
+    const double pAp = 2.0 * block_sum((double)pAp_t, red);
     if (!(pAp > 0.0)) {
         if (threadIdx.x == 0) st.cg_stop = 1;
         return;
     }
-    const double alpha = rz / pAp;
-    double rzn = 0.0;
+    const float alpha = (float)(rz / pAp);
+    float rzn_t = 0.f;
     for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) {
-        const double lam = 0.5 * (double)a.rho[blk / N] + mu;
+        const float lam = 0.5f * a.rho[blk / N] + mu;
         Blk x = load_blk(a.x + off, blk), r = load_blk(a.r + off, blk);
         const Blk p = load_blk(a.p + off, blk), ap = load_blk(a.Ap + off, blk);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
-            x.v[i] = (float)((double)x.v[i] + alpha * (double)p.v[i]);
-            r.v[i] = (float)((double)r.v[i] - alpha * (double)ap.v[i]);
+            x.v[i] = fmaf(alpha, p.v[i], x.v[i]);
+            r.v[i] = fmaf(-alpha, ap.v[i], r.v[i]);
         }
         const Blk z = precond(r, G + (size_t)blk * 4, lam);
         store_blk(a.x + off, blk, x);
         store_blk(a.r + off, blk, r);
         store_blk(a.z + off, blk, z);
-        rzn += dot_blk(r, z);
+        rzn_t += dot_blk(r, z);
     }
-    rzn = 2.0 * block_sum(rzn, red);
-    const double beta = rzn / rz;
+    const double rzn = 2.0 * block_sum((double)rzn_t, red);
+    const float beta = (float)(rzn / rz);
     for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) {
         const Blk z = load_blk(a.z + off, blk);
         Blk p = load_blk(a.p + off, blk);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) p.v[i] = (float)((double)z.v[i] + beta * (double)p.v[i]);
+        for (int i = 0; i < 8; ++i) p.v[i] = fmaf(beta, p.v[i], z.v[i]);
         store_blk(a.p + off, blk, p);
     }
     if (threadIdx.x == 0) {
@@ -370,7 +478,7 @@ __global__ void __launch_bounds__(LM_THREADS) k_lm_trial(const LMArgs a) {
     const size_t off = (size_t)agent * KN * 8;
     AgentState& st = a.st[agent];
     const double mu = st.mu;
-    double xr = 0.0, xx = 0.0;
+    float xr_t = 0.f, xx_t = 0.f;
     for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) {
         const Blk x = load_blk(a.x + off, blk), r = load_blk(a.r + off, blk), gr = load_blk(a.grad + off, blk);
         const Blk j = load_blk(a.J + off, blk);
@@ -378,13 +486,13 @@ __global__ void __launch_bounds__(LM_THREADS) k_lm_trial(const LMArgs a) {
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             jt.v[i] = j.v[i] + x.v[i];
-            xr += (double)x.v[i] * ((double)r.v[i] - (double)gr.v[i]);
-            xx += (double)x.v[i] * (double)x.v[i];
+            xr_t = fmaf(x.v[i], r.v[i] - gr.v[i], xr_t);
+            xx_t = fmaf(x.v[i], x.v[i], xx_t);
         }
         store_blk(a.Jt + off, blk, jt);
     }
-    xr = block_sum(xr, red);
-    xx = block_sum(xx, red);
+    const double xr = block_sum((double)xr_t, red);
+    const double xx = block_sum((double)xx_t, red);
     // pred = 1/2 h(x, b + r) + mu/2 h(x, x) with b = -grad, h = 2 * dot
     if (threadIdx.x == 0) st.pred = xr + mu * xx;
 }
