@@ -37,7 +37,10 @@ UNIT = "vis*dir*iter/s"
 
 # DRAM traffic per launch of the dominant sweep kernel from one ncu capture; valid only for the
 # kernel source it was taken on (sha256 prefix of sweep.cu), else reported as null.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {  # profiles/sweep_kernels_lofar_n62_k5.md (dram__bytes_read.sum + dram__bytes_write.sum)
+    ("sweep_hessvec", "8e587c1134b3"): 269.0e6,
+    ("sweep_residual", "8e587c1134b3"): 468.0e6,
+}
 
 
 def peaks():
