@@ -56,6 +56,14 @@ enum {
 
 typedef struct calib_ctx calib_ctx;
 
+/* How the LM/PCG passes of the J-update read the data (calib_options.formulation). Both compute
+ * the same quantities (the sums over the samples of a baseline, Section 2):
+ *  CALIB_FORM_STATISTICS  per-baseline sufficient statistics U_k = sum_t conj(c_tk) V_t and
+ *                         S_kl = sum_t conj(c_tk) c_tl, formed once per data set (exact because
+ *                         C = c I_2 and J is constant over an interval); passes no longer depend on T;
+ *  CALIB_FORM_DIRECT      every pass streams the visibilities and coherencies sample by sample. */
+enum { CALIB_FORM_STATISTICS = 0, CALIB_FORM_DIRECT = 1 };
+
 typedef struct {
     int n_intervals;                   /* I >= 1 (default 1) */
     int n_samples;                     /* T >= 1: samples per agent when samples_per_agent is NULL */
@@ -64,6 +72,7 @@ typedef struct {
     int n_cg;                          /* PCG steps per LM step (default 4) */
     int chunk_diagonals;               /* baseline diagonals per CTA in the sweeps; 0 = automatic */
     void* cuda_stream;                 /* cudaStream_t to run on; NULL = the library creates one */
+    int formulation;                   /* CALIB_FORM_STATISTICS (default) or CALIB_FORM_DIRECT */
 } calib_options;
 
 /* One record per C-ADMM iteration (Section 4 definitions, summed/averaged over all intervals):
@@ -160,7 +169,9 @@ int calib_hessvec(calib_ctx* ctx, const void* J, const void* eta, void* out, int
 int calib_sync(calib_ctx* ctx);
 
 /* Per-kernel timing over the following calib_admm_iter calls (CUDA events recorded
- * on the library stream around every launch of the sweep kernels when enabled).
+ * on the library stream around every launch of the sweep kernels when enabled). Kinds:
+ * sweep_residual (direct residual/trial), sweep_hessvec (direct Hessian), stats_hessvec and
+ * stats_trial (sufficient-statistics passes); bytes_per_launch are the algorithmic bytes.
  * names/ms/launches receive up to cap entries; returns the number of kernel kinds. */
 int calib_profile_enable(calib_ctx* ctx, int on);
 int calib_profile_read(calib_ctx* ctx, int cap, const char** names, double* total_ms,

@@ -14,6 +14,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libcalib.so")
 
+CALIB_FORM_STATISTICS, CALIB_FORM_DIRECT = 0, 1
 CALIB_OK, CALIB_EINVAL, CALIB_ERANK, CALIB_ENOMEM, CALIB_ECUDA, CALIB_ETIMEOUT, CALIB_ENUMERIC, CALIB_ESTATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 
@@ -27,7 +28,8 @@ EXPORTED = [
 
 class CalibOptions(C.Structure):
     _fields_ = [("n_intervals", C.c_int), ("n_samples", C.c_int), ("samples_per_agent", C.POINTER(C.c_int32)),
-                ("n_lm", C.c_int), ("n_cg", C.c_int), ("chunk_diagonals", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("n_lm", C.c_int), ("n_cg", C.c_int), ("chunk_diagonals", C.c_int), ("cuda_stream", C.c_void_p),
+                ("formulation", C.c_int)]
 
 
 class CalibStats(C.Structure):
@@ -118,7 +120,7 @@ def calib_default_options() -> CalibOptions:
 
 
 def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, samples_per_agent=None,
-               n_lm=10, n_cg=4, chunk_diagonals=0, cuda_stream=None):
+               n_lm=10, n_cg=4, chunk_diagonals=0, cuda_stream=None, formulation=CALIB_FORM_STATISTICS):
     lib = load()
     pq_a = np.ascontiguousarray(pq, dtype=np.int32)
     fr = np.ascontiguousarray(freqs_hz, dtype=np.float64)
@@ -127,6 +129,7 @@ def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, sa
     opt = calib_default_options()
     opt.n_intervals, opt.n_samples, opt.n_lm, opt.n_cg = n_intervals, n_samples, n_lm, n_cg
     opt.chunk_diagonals = chunk_diagonals
+    opt.formulation = formulation
     spa = None
     if samples_per_agent is not None:
         spa = np.ascontiguousarray(samples_per_agent, dtype=np.int32)

@@ -7,6 +7,10 @@
 //   part_cost [A][n_chunks]  float64 partial data cost
 //   Z, Zprev  [I][K][M][N][8] float64
 //
+// Sufficient statistics of a slot (C = c I_2 and J constant over the interval make them exact):
+//   U_k = sum_t conj(c_tk) V_t (K 2x2 blocks), S_kl = sum_t conj(c_tk) c_tl (K x K Hermitian, upper
+//   triangle packed row-major: entry (k,l), k <= l, at k*K - k*(k-1)/2 + (l-k)).
+//
 // Baselines are re-laid out per agent by circulant diagonal: diagonal d (1 <= d <= N/2) holds
 // the pairs (i, (i+d) mod N); within one diagonal every station is the first element of at most
 // one pair and the second element of at most one pair, which makes the per-station reductions
@@ -35,6 +39,8 @@ enum StatusBits : int { STATUS_TIMEOUT = 1, STATUS_NONFINITE = 2 };
 struct DiagDesc {     // one per (agent, diagonal)
     long long voff;   // float2 offset of the V block
     long long coff;   // float2 offset of the C block
+    long long uoff;   // float2 offset of the U block [n_pad][K][4] (sufficient statistics)
+    long long soff;   // float2 offset of the S block [n_pad][K(K+1)/2] (sufficient statistics)
     int slot_off;     // global index of the first slot of this diagonal in the slot arrays
     int n;            // active (unflagged) slots
     int n_pad;        // padded slot count (multiple of 4, >= n)
@@ -77,8 +83,11 @@ struct LMArgs {
     AgentState* st;
     const float* rho;       // [K]
     const DiagDesc* desc; const int* slot; const float* spow;   // for the Jacobi blocks
+    const int* inc_off;     // [A][N+1] start of each station's incidence list in inc
+    const int2* inc;        // (global slot, other station) per incident baseline, slot order
     int A, N, K, D;
     double tau;
+    int cost_from_decrease;  // trial cost g(J') = g(J) - decrease (statistics sweeps carry no cost)
 };
 
 struct ConsArgs {
@@ -142,6 +151,24 @@ cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s);
 cudaError_t launch_coh_power(const float2* C, const DiagDesc* desc, const int* T, float* spow,
                              int A, int D, int K, cudaStream_t s);
 cudaError_t launch_check_finite(const float* x, long long n, int* status, cudaStream_t s);
+cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc,
+                            const int* T, int A, int D, int K, cudaStream_t s);
+
+// ---- launchers (ss.cu): sweeps on the sufficient statistics
+struct SSArgs {
+    const float2* U; const float2* S;
+    const DiagDesc* desc; const int* slot;
+    const float* J; const float* eta;   // eta: direction (Hessian) or LM step x (trial)
+    float* part; double* part_dcost; int* status;
+    int A, N, K, D, n_chunks, chunk_diags, slots_max;
+    // Finishing the agent's LM/PCG step in the last CTA to complete its chunks:
+    int fuse;        // 0: sweep only; 1: Hessian -> PCG step (+ LM trial point if last_cg), trial -> LM accept
+    int last_cg;     // this Hessian sweep feeds the last PCG step of the LM step
+    int* arrive;     // [A] chunk arrival counters (zero between launches)
+    LMArgs lm;
+};
+cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, cudaStream_t s);
+cudaError_t prepare_ss_kernels();
 
 // One-time kernel attribute set-up (dynamic shared memory limits); call before any capture.
 cudaError_t prepare_sweep_kernels();

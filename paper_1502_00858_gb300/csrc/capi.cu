@@ -39,7 +39,7 @@ cudaError_t dalloc(T** p, size_t count) {
 
 struct ProfPair {
     cudaEvent_t a, b;
-    int kind;  // 0 residual or trial sweep, 1 Hessian sweep
+    int kind;  // 0 residual or trial sweep, 1 Hessian sweep, 2 statistics Hessian, 3 statistics trial
 };
 
 struct GraphEntry {
@@ -68,14 +68,20 @@ struct calib_ctx {
     // layout (depends on flags)
     std::vector<DiagDesc> desc_h;
     std::vector<int> slot_h, slot_b_h;
+    std::vector<int> inc_off_h;
+    std::vector<int2> inc_h;
     long long int_v = 0, int_c = 0;             // internal totals (float2)
-    double alg_bytes_res = 0, alg_bytes_hv = 0; // algorithmic bytes per sweep launch
+    long long int_u = 0, int_s = 0;             // sufficient-statistics totals (float2)
+    double alg_bytes[4] = {0, 0, 0, 0};         // algorithmic bytes per launch of each sweep kind
     std::vector<uint8_t> flags_h;
 
     // device
-    float2 *V = nullptr, *C = nullptr;
+    float2 *V = nullptr, *C = nullptr, *ssU = nullptr, *ssS = nullptr;
+    int formulation = 0;  // 0 sufficient statistics, 1 direct
+    bool ss_dirty = true;
     DiagDesc* desc = nullptr;
-    int *slot = nullptr, *slot_b = nullptr, *T_d = nullptr;
+    int *slot = nullptr, *slot_b = nullptr, *T_d = nullptr, *inc_off = nullptr;
+    int2* inc = nullptr;
     float* spow = nullptr;
     long long *vis_off_d = nullptr, *coh_off_d = nullptr;
     float *J = nullptr, *Jt = nullptr, *Y = nullptr, *BZ = nullptr, *gradg = nullptr, *grad = nullptr;
@@ -93,6 +99,7 @@ struct calib_ctx {
     int max_iters = 0;
     int* iter_counter = nullptr;
     int* status = nullptr;
+    int* arrive = nullptr;
     double* evL = nullptr;
     double* evG = nullptr;
     void* staging = nullptr;
@@ -104,8 +111,8 @@ struct calib_ctx {
     std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;
     long long launches = 0;
     bool profiling = false;
-    double prof_ms[2] = {0, 0};
-    long long prof_n[2] = {0, 0};
+    double prof_ms[4] = {0, 0, 0, 0};
+    long long prof_n[4] = {0, 0, 0, 0};
 };
 
 namespace {
@@ -158,11 +165,37 @@ LMArgs lm_args(calib_ctx* c) {
     a.desc = c->desc;
     a.slot = c->slot;
     a.spow = c->spow;
+    a.inc_off = c->inc_off;
+    a.inc = c->inc;
     a.A = c->A;
     a.N = c->N;
     a.K = c->K;
     a.D = c->D;
     a.tau = 1e-3;
+    a.cost_from_decrease = c->formulation == 0 ? 1 : 0;
+    return a;
+}
+
+SSArgs ss_args(calib_ctx* c, const float* J, const float* eta) {
+    SSArgs a{};
+    a.lm = lm_args(c);
+    a.arrive = c->arrive;
+    a.U = c->ssU;
+    a.S = c->ssS;
+    a.desc = c->desc;
+    a.slot = c->slot;
+    a.J = J;
+    a.eta = eta;
+    a.part = c->part;
+    a.part_dcost = c->part_dcost;
+    a.status = c->status;
+    a.A = c->A;
+    a.N = c->N;
+    a.K = c->K;
+    a.D = c->D;
+    a.n_chunks = c->n_chunks;
+    a.chunk_diags = c->chunk_diags;
+    a.slots_max = c->slots_max;
     return a;
 }
 
@@ -234,6 +267,10 @@ void free_layout(calib_ctx* c) {
     cudaFree(c->slot); c->slot = nullptr;
     cudaFree(c->slot_b); c->slot_b = nullptr;
     cudaFree(c->spow); c->spow = nullptr;
+    cudaFree(c->ssU); c->ssU = nullptr;
+    cudaFree(c->ssS); c->ssS = nullptr;
+    cudaFree(c->inc_off); c->inc_off = nullptr;
+    cudaFree(c->inc); c->inc = nullptr;
 }
 
 void clear_graphs(calib_ctx* c) {
@@ -255,9 +292,10 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     c->desc_h.assign((size_t)A * D, DiagDesc{});
     c->slot_h.clear();
     c->slot_b_h.clear();
-    long long voff = 0, coff = 0;
+    long long voff = 0, coff = 0, uoff = 0, soff = 0;
+    const int KK = K * (K + 1) / 2;
     int smax = 4;
-    double alg_res = 0, alg_hv = 0;
+    double alg_res = 0, alg_hv = 0, alg_ssh = 0, alg_sst = 0;
     for (int a = 0; a < A; ++a) {
         for (int d = 1; d <= D; ++d) {
             DiagDesc& dd = c->desc_h[(size_t)a * D + d - 1];
@@ -279,18 +317,49 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
             dd.n_pad = (n + 3) / 4 * 4;
             dd.voff = voff;
             dd.coff = coff;
+            dd.uoff = uoff;
+            dd.soff = soff;
             voff += (long long)c->T[a] * dd.n_pad * 4;
             coff += (long long)c->T[a] * dd.n_pad * K;
+            uoff += (long long)dd.n_pad * K * 4;
+            soff += (long long)dd.n_pad * KK;
             smax = std::max(smax, dd.n_pad);
             alg_res += (double)n * c->T[a] * (32.0 + 8.0 * K);
             alg_hv += (double)n * c->T[a] * (8.0 * K);
+            alg_ssh += (double)n * 8.0 * KK;
+            alg_sst += (double)n * (32.0 * K + 8.0 * KK);
+        }
+    }
+    // station-incidence lists per agent (global slot, other station), in slot order
+    c->inc_off_h.assign((size_t)A * (N + 1), 0);
+    c->inc_h.assign(2 * c->slot_h.size(), int2{0, 0});
+    {
+        size_t pos = 0;
+        for (int a = 0; a < A; ++a) {
+            const int s0 = c->desc_h[(size_t)a * D].slot_off;
+            const int s1 = (a + 1 < A) ? c->desc_h[(size_t)(a + 1) * D].slot_off : (int)c->slot_h.size();
+            std::vector<std::vector<int2>> lists(N);
+            for (int s = s0; s < s1; ++s) {
+                const int f = c->slot_h[s] & 0xff, sc = (c->slot_h[s] >> 8) & 0xff;
+                lists[f].push_back(int2{s, sc});
+                lists[sc].push_back(int2{s, f});
+            }
+            for (int p = 0; p < N; ++p) {
+                c->inc_off_h[(size_t)a * (N + 1) + p] = (int)pos;
+                for (const int2& e : lists[p]) c->inc_h[pos++] = e;
+            }
+            c->inc_off_h[(size_t)a * (N + 1) + N] = (int)pos;
         }
     }
     c->int_v = voff;
     c->int_c = coff;
+    c->int_u = uoff;
+    c->int_s = soff;
     c->slots_max = smax;
-    c->alg_bytes_res = alg_res;
-    c->alg_bytes_hv = alg_hv;
+    c->alg_bytes[0] = alg_res;
+    c->alg_bytes[1] = alg_hv;
+    c->alg_bytes[2] = alg_ssh;
+    c->alg_bytes[3] = alg_sst;
     c->TT_res = sweep_tile_samples(smax, K, false);
     c->TT_hv = sweep_tile_samples(smax, K, true);
     if (sweep_threads(smax) > 512) return fail(CALIB_EINVAL, "too many stations for one CTA per diagonal");
@@ -304,6 +373,13 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     CK(dalloc(&c->slot, c->slot_h.size()));
     CK(dalloc(&c->slot_b, c->slot_b_h.size()));
     CK(dalloc(&c->spow, c->slot_h.size() * (size_t)K));
+    CK(dalloc(&c->inc_off, c->inc_off_h.size()));
+    CK(dalloc(&c->inc, c->inc_h.size()));
+    CK(cudaMemcpy(c->inc_off, c->inc_off_h.data(), c->inc_off_h.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!c->inc_h.empty())
+        CK(cudaMemcpy(c->inc, c->inc_h.data(), c->inc_h.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CK(dalloc(&c->ssU, (size_t)c->int_u));
+    CK(dalloc(&c->ssS, (size_t)c->int_s));
     CK(cudaMemcpy(c->desc, c->desc_h.data(), c->desc_h.size() * sizeof(DiagDesc), cudaMemcpyHostToDevice));
     if (!c->slot_h.empty()) {
         CK(cudaMemcpy(c->slot, c->slot_h.data(), c->slot_h.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -314,6 +390,7 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     clear_graphs(c);
     c->data_set = false;
     c->coh_set = false;
+    c->ss_dirty = true;
     return CALIB_OK;
 }
 
@@ -366,16 +443,24 @@ struct Enq {
         if (err == cudaSuccess && e != cudaSuccess) err = e;
         ge->kernels += 1;
     }
-    void sweep(int mode, const float* J, const float* eta) {
+    void sweep(int mode, const float* J, const float* eta, int fuse = 0, int last_cg = 0) {
         ProfPair pp{};
         const bool prof = c->profiling;
+        const bool ss = c->formulation == 0 && mode != SWEEP_RESIDUAL;
         if (prof) {
             cudaEventCreate(&pp.a);
             cudaEventCreate(&pp.b);
-            pp.kind = mode == SWEEP_HESSVEC ? 1 : 0;
+            pp.kind = ss ? (mode == SWEEP_HESSVEC ? 2 : 3) : (mode == SWEEP_HESSVEC ? 1 : 0);
             cudaEventRecordWithFlags(pp.a, c->stream, cudaEventRecordExternal);
         }
-        ok(launch_sweep(sweep_args(c, mode, J, eta), mode, c->stream));
+        if (ss) {
+            SSArgs sa = ss_args(c, J, eta);
+            sa.fuse = fuse;
+            sa.last_cg = last_cg;
+            ok(launch_ss_sweep(sa, mode == SWEEP_HESSVEC, c->stream));
+        } else {
+            ok(launch_sweep(sweep_args(c, mode, J, eta), mode, c->stream));
+        }
         if (prof) {
             cudaEventRecordWithFlags(pp.b, c->stream, cudaEventRecordExternal);
             ge->prof.push_back(pp);
@@ -393,14 +478,15 @@ void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
     } else {
         q.ok(launch_lm_eval(la, LM_BEGIN_REUSE, c->stream));
     }
+    const bool fused = c->formulation == 0;  // statistics sweeps finish the LM/PCG steps themselves
     for (int l = 0; l < c->n_lm; ++l) {
         for (int k = 0; k < c->n_cg; ++k) {
-            q.sweep(SWEEP_HESSVEC, c->J, c->p);
-            q.ok(launch_cg_step(la, c->stream));
+            q.sweep(SWEEP_HESSVEC, c->J, c->p, fused ? 1 : 0, k == c->n_cg - 1 ? 1 : 0);
+            if (!fused) q.ok(launch_cg_step(la, c->stream));
         }
-        q.ok(launch_lm_trial(la, c->stream));
-        q.sweep(SWEEP_TRIAL, c->J, c->x);
-        q.ok(launch_lm_eval(la, LM_ACCEPT, c->stream));
+        if (!fused) q.ok(launch_lm_trial(la, c->stream));
+        q.sweep(SWEEP_TRIAL, c->J, c->x, fused ? 1 : 0);
+        if (!fused) q.ok(launch_lm_eval(la, LM_ACCEPT, c->stream));
     }
     if (gauge) q.ok(launch_gauge(ca, c->stream));
     q.ok(launch_zupdate(ca, c->stream));
@@ -437,6 +523,7 @@ void calib_default_options(calib_options* opt) {
     opt->n_cg = 4;
     opt->chunk_diagonals = 0;
     opt->cuda_stream = nullptr;
+    opt->formulation = CALIB_FORM_STATISTICS;
 }
 
 int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* pq, int n_dirs, int n_freqs,
@@ -457,6 +544,8 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     if (P < M) return fail(CALIB_ERANK, "need at least as many frequencies as basis terms (P >= M)");
     if (opt.n_intervals < 1) return fail(CALIB_EINVAL, "n_intervals must be >= 1");
     if (opt.n_lm < 1 || opt.n_cg < 1) return fail(CALIB_EINVAL, "n_lm and n_cg must be >= 1");
+    if (opt.formulation != CALIB_FORM_STATISTICS && opt.formulation != CALIB_FORM_DIRECT)
+        return fail(CALIB_EINVAL, "formulation must be CALIB_FORM_STATISTICS or CALIB_FORM_DIRECT");
     std::vector<char> seen((size_t)N * N, 0);
     for (int b = 0; b < B; ++b) {
         const int p = pq[2 * b], q = pq[2 * b + 1];
@@ -483,6 +572,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     c->D = N / 2;
     c->n_lm = opt.n_lm;
     c->n_cg = opt.n_cg;
+    c->formulation = opt.formulation;
     c->pq.assign(pq, pq + 2 * (size_t)B);
     c->freqs.assign(freqs_hz, freqs_hz + P);
     c->basis.assign(basis, basis + (size_t)P * M);
@@ -522,6 +612,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     cudaError_t pe = prepare_sweep_kernels();
     if (pe == cudaSuccess) pe = prepare_lm_kernels();
     if (pe == cudaSuccess) pe = prepare_data_kernels();
+    if (pe == cudaSuccess) pe = prepare_ss_kernels();
     if (pe != cudaSuccess) return bail(fail(CALIB_ECUDA, std::string("kernel set-up: ") + cudaGetErrorString(pe)));
 
     const size_t vec = (size_t)A * K * N * 8;
@@ -539,6 +630,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     okm = okm && dalloc(&c->freqs_d, (size_t)P) == cudaSuccess && dalloc(&c->rho_d, (size_t)K) == cudaSuccess;
     okm = okm && dalloc(&c->st, (size_t)A) == cudaSuccess && dalloc(&c->prim, (size_t)A * K) == cudaSuccess;
     okm = okm && dalloc(&c->dual2, (size_t)c->I * K) == cudaSuccess;
+    okm = okm && dalloc(&c->arrive, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->iter_counter, 1) == cudaSuccess && dalloc(&c->status, 1) == cudaSuccess;
     okm = okm && dalloc(&c->evL, (size_t)A) == cudaSuccess && dalloc(&c->evG, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess;
@@ -611,6 +703,7 @@ int calib_set_data(calib_ctx* c, const void* vis, const void* coh, const uint8_t
     ia.is_vis = 1;
     CK(launch_ingest(ia, c->stream));
     c->launches += 2;
+    c->ss_dirty = true;
     if (coh) {
         const void* dc = nullptr;
         rc = stage_in(c, coh, (size_t)c->user_c * sizeof(float2), ptr_kind, &dc);
@@ -671,6 +764,7 @@ int calib_predict(calib_ctx* c, const double* uvw_m, const double* sky, int n_sr
     CK(launch_predict(pa, c->stream));
     CK(launch_coh_power(c->C, c->desc, c->T_d, c->spow, c->A, c->D, c->K, c->stream));
     c->launches += 2;
+    c->ss_dirty = true;
     c->coh_set = true;
     c->need_eval = true;
     if (ptr_kind == 0) CK(cudaStreamSynchronize(c->stream));
@@ -747,6 +841,12 @@ int calib_admm_iter(calib_ctx* c, int n_iters, calib_stats* hist) {
     if (rc) return rc;
     CK(cudaMemsetAsync(c->iter_counter, 0, sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->arrive, 0, (size_t)c->A * sizeof(int), c->stream));
+    if (c->formulation == 0 && c->ss_dirty) {
+        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->T_d, c->A, c->D, c->K, c->stream));
+        c->launches += 1;
+        c->ss_dirty = false;
+    }
     const auto key = std::make_tuple(n_iters, c->need_eval ? 1 : 0, c->cold ? 1 : 0, c->profiling ? 1 : 0);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
@@ -874,23 +974,24 @@ int calib_sync(calib_ctx* c) {
 int calib_profile_enable(calib_ctx* c, int on) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     c->profiling = on != 0;
-    c->prof_ms[0] = c->prof_ms[1] = 0.0;
-    c->prof_n[0] = c->prof_n[1] = 0;
+    for (int i = 0; i < 4; ++i) {
+        c->prof_ms[i] = 0.0;
+        c->prof_n[i] = 0;
+    }
     return CALIB_OK;
 }
 
 int calib_profile_read(calib_ctx* c, int cap, const char** names, double* total_ms, long long* launches,
                        double* bytes_per_launch) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
-    static const char* kNames[2] = {"sweep_residual", "sweep_hessvec"};
-    const double bytes[2] = {c->alg_bytes_res, c->alg_bytes_hv};
-    for (int i = 0; i < 2 && i < cap; ++i) {
+    static const char* kNames[4] = {"sweep_residual", "sweep_hessvec", "stats_hessvec", "stats_trial"};
+    for (int i = 0; i < 4 && i < cap; ++i) {
         if (names) names[i] = kNames[i];
         if (total_ms) total_ms[i] = c->prof_ms[i];
         if (launches) launches[i] = c->prof_n[i];
-        if (bytes_per_launch) bytes_per_launch[i] = bytes[i];
+        if (bytes_per_launch) bytes_per_launch[i] = c->alg_bytes[i];
     }
-    return 2;
+    return 4;
 }
 
 long long calib_launch_count(calib_ctx* c) { return c ? c->launches : 0; }
@@ -907,7 +1008,7 @@ void calib_destroy(calib_ctx* c) {
                     (void*)c->evJ, (void*)c->evE, (void*)c->evOut, (void*)c->part, (void*)c->part_cost, (void*)c->part_dcost,
                     (void*)c->Z, (void*)c->Zprev, (void*)c->basis_d, (void*)c->Pinv_d, (void*)c->freqs_d,
                     (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->dual2, (void*)c->stats, (void*)c->iter_counter,
-                    (void*)c->status, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
+                    (void*)c->status, (void*)c->arrive, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
                     (void*)c->coh_off_d, c->staging})
         if (p) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

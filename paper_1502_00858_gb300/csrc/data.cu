@@ -154,6 +154,47 @@ __global__ void k_coh_power(const float2* C, const DiagDesc* desc, const int* T,
     }
 }
 
+// Sufficient statistics per (agent, diagonal): thread (slot g, entry e) accumulates
+// U_k[e] = sum_t conj(c_tk) V_t[e] for all k, and its share of the packed S_kl = sum_t conj(c_tk) c_tl.
+__global__ void __launch_bounds__(256) k_ss_stats(const float2* V, const float2* C, float2* U, float2* S,
+                                                  const DiagDesc* desc, const int* T, int D, int K) {
+    const int d = blockIdx.x, agent = blockIdx.y;
+    const DiagDesc dsc = desc[(size_t)agent * D + d];
+    const int Ta = T[agent];
+    const int KK = K * (K + 1) / 2;
+    for (int base = 0; base < dsc.n_pad; base += blockDim.x / 4) {
+        const int g = base + (threadIdx.x >> 2), e = threadIdx.x & 3;
+        if (g >= dsc.n_pad) continue;
+        float2 u[MAX_K];
+        for (int k = 0; k < K; ++k) u[k] = make_float2(0.f, 0.f);
+        for (int t = 0; t < Ta; ++t) {
+            const float2 v = V[dsc.voff + ((size_t)t * dsc.n_pad + g) * 4 + e];
+            const float2* cp = C + dsc.coff + ((size_t)t * dsc.n_pad + g) * K;
+            for (int k = 0; k < K; ++k) {
+                const float2 c = cp[k];
+                u[k].x = fmaf(c.x, v.x, fmaf(c.y, v.y, u[k].x));
+                u[k].y = fmaf(c.x, v.y, fmaf(-c.y, v.x, u[k].y));
+            }
+        }
+        float2* uo = U + dsc.uoff + (size_t)g * K * 4;
+        for (int k = 0; k < K; ++k) uo[k * 4 + e] = u[k];
+        // packed S entries idx = e, e + 4, ...
+        for (int idx = e; idx < KK; idx += 4) {
+            int k = 0, rem = idx;
+            while (rem >= K - k) { rem -= K - k; ++k; }
+            const int l = k + rem;
+            float sr = 0.f, si = 0.f;
+            for (int t = 0; t < Ta; ++t) {
+                const float2* cp = C + dsc.coff + ((size_t)t * dsc.n_pad + g) * K;
+                const float2 ck = cp[k], cl = cp[l];
+                sr = fmaf(ck.x, cl.x, fmaf(ck.y, cl.y, sr));   // conj(c_k) c_l
+                si = fmaf(ck.x, cl.y, fmaf(-ck.y, cl.x, si));
+            }
+            S[dsc.soff + (size_t)g * KK + idx] = make_float2(sr, si);
+        }
+    }
+}
+
 __global__ void k_check_finite(const float* x, long long n, int* status) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long stride = (long long)gridDim.x * blockDim.x;
@@ -192,6 +233,13 @@ cudaError_t launch_coh_power(const float2* C, const DiagDesc* desc, const int* T
     k_coh_power<<<A, 256, 0, s>>>(C, desc, T, spow, D, K);
     return cudaGetLastError();
 }
+cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc,
+                            const int* T, int A, int D, int K, cudaStream_t s) {
+    dim3 grid(D, A);
+    k_ss_stats<<<grid, 256, 0, s>>>(V, C, U, S, desc, T, D, K);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_check_finite(const float* x, long long n, int* status, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;

@@ -89,14 +89,16 @@ __device__ __forceinline__ float2 shfl2(float2 v, int src) {
 
 enum { M_RESID = 0, M_HV = 1, M_TRIAL = 2 };
 
-template <int KB, int MODE>
+// KB: register bucket; EXACT: K == KB, so loop bounds and strides over K are constants.
+template <int KB, int MODE, bool EXACT>
 __global__ void __launch_bounds__(512) k_sweep(const SweepArgs a, const int stage_bytes) {
     constexpr bool HV = MODE == M_HV;
     constexpr bool TR = MODE == M_TRIAL;
     extern __shared__ __align__(128) unsigned char smem[];
     const int agent = blockIdx.y;
     const int chunk = blockIdx.x;
-    const int N = a.N, K = a.K, D = a.D;
+    const int N = a.N, D = a.D;
+    const int K = EXACT ? KB : a.K;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int g = tid >> 2, e = tid & 3;
     const int lane = tid & 31, gbase = lane & ~3;
@@ -329,13 +331,18 @@ __global__ void __launch_bounds__(512) k_sweep(const SweepArgs a, const int stag
 
 template <int KB, int HV>
 cudaError_t prepare_kb() {
-    return cudaFuncSetAttribute(k_sweep<KB, HV>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep<KB, HV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_sweep<KB, HV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
 
 template <int KB, int HV>
 cudaError_t launch_kb(const SweepArgs& a, int threads, size_t smem, int stage_bytes, cudaStream_t s) {
     dim3 grid(a.n_chunks, a.A);
-    k_sweep<KB, HV><<<grid, threads, smem, s>>>(a, stage_bytes);
+    if (a.K == KB)
+        k_sweep<KB, HV, true><<<grid, threads, smem, s>>>(a, stage_bytes);
+    else
+        k_sweep<KB, HV, false><<<grid, threads, smem, s>>>(a, stage_bytes);
     return cudaGetLastError();
 }
 

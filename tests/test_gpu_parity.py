@@ -10,10 +10,13 @@ gauge of each direction: the data term is exactly flat along it (C = c I_2, Eq. 
 only the penalty curves it, with Hessian rho/2 against ~sum_t |c|^2 |J|^2 for the data.
 Float32 residuals carry an error ~eps |V| per element, so the gauge component of the
 gradient is known to ~eps |V| |J| sum(T) / (rho/2 |dJ_gauge|), a few per cent on these
-inputs; the dual is compared at 15 % relative, with an absolute floor of 1e-5 of the
-solution scale ||Z^1|| / sqrt(4MN) (the first record) where the iteration has converged
-and float32 stops resolving the difference of consecutive Z. With one LM step per
-J-update the gauge mode is not resolved on either side and all four records agree at 1e-4.
+inputs. Z is the least-squares fit of Eq. Zest, so differences in J reach Z amplified by
+||(sum_i b_i b_i^T)^-1 B^T||_2: 1.9 for the Bernstein basis of the LOFAR-shaped case but 20.7
+for the ordinary polynomial over the narrow band of the tiny case. The dual is therefore
+compared at max(15 %, 1.5 % x that amplification) relative, with an absolute floor of 1e-5 of
+the solution scale ||Z^1|| / sqrt(4MN) (the first record) where the iteration has converged
+and float32 stops resolving the difference of consecutive Z. With one LM step per J-update
+the gauge mode is not resolved on either side and all four records agree at 1e-4.
 """
 import math
 
@@ -21,12 +24,14 @@ import numpy as np
 import pytest
 
 from oracle import admm as O
-from paper_1502_00858_gb300 import Calibrator
+from paper_1502_00858_gb300 import Calibrator, capi
 from synth import make_problem, user_layout
 
 pytestmark = pytest.mark.gpu
 
 REL_ADMM = 1e-4
+FORMS = {"statistics": capi.CALIB_FORM_STATISTICS, "direct": capi.CALIB_FORM_DIRECT}
+_ORACLE_CACHE = {}
 
 
 def cn(rng, *shape):
@@ -141,30 +146,34 @@ def test_predict_matches_oracle(lib, case):
         assert np.all(blk[~keep] == 0)
 
 
-def run_both(lib, prob, n_iter, n_lm=10, n_cg=4):
-    cal = calibrator(lib, prob, n_lm=n_lm, n_cg=n_cg)
+def run_both(lib, prob, n_iter, n_lm=10, n_cg=4, form="statistics"):
+    cal = calibrator(lib, prob, n_lm=n_lm, n_cg=n_cg, formulation=FORMS[form])
     hist = cal.iterate(n_iter)
     ref = O.admm(rounded(prob), n_iter, n_lm=n_lm, n_cg=n_cg)["hist"]
     return cal, hist, ref
 
 
+@pytest.mark.parametrize("form", sorted(FORMS))
 @pytest.mark.parametrize("case", ["tiny_n8_k1", "ragged_n13_k3", "n2_single_baseline"])
-def test_admm_history_matches_oracle(lib, case):
+def test_admm_history_matches_oracle(lib, case, form):
     prob = CASES[case]()
     n_iter = 10 if case == "tiny_n8_k1" else 4
-    _, hist, ref = run_both(lib, prob, n_iter)
+    _, hist, ref = run_both(lib, prob, n_iter, form=form)
     np.testing.assert_allclose(hist["objective"], ref["objective"], rtol=REL_ADMM)
     np.testing.assert_allclose(hist["resid_norm"], ref["resid_norm"], rtol=REL_ADMM)
     np.testing.assert_allclose(hist["primal"], ref["primal"], rtol=1e-3, atol=1e-7)
-    np.testing.assert_allclose(hist["dual"], ref["dual"], rtol=0.15, atol=1e-5 * ref["dual"][0])
+    basis = prob["basis"]
+    amp = np.linalg.norm(np.linalg.pinv(basis.T @ basis) @ basis.T, 2)
+    np.testing.assert_allclose(hist["dual"], ref["dual"], rtol=max(0.15, 0.015 * amp), atol=1e-5 * ref["dual"][0])
 
 
+@pytest.mark.parametrize("form", sorted(FORMS))
 @pytest.mark.parametrize("case,n_cg", [("n3_k2", 1), ("tiny_n8_k1", 4), ("ragged_n13_k3", 4)])
-def test_admm_one_lm_step_matches_all_records(lib, case, n_cg):
+def test_admm_one_lm_step_matches_all_records(lib, case, n_cg, form):
     """n_lm = 1 (and n_cg = 1: one preconditioned steepest-descent step): the gauge mode is
     not resolved, so primal and dual residuals agree at 1e-4 as well."""
     prob = CASES[case]()
-    _, hist, ref = run_both(lib, prob, 3, n_lm=1, n_cg=n_cg)
+    _, hist, ref = run_both(lib, prob, 3, n_lm=1, n_cg=n_cg, form=form)
     for key in ("objective", "resid_norm", "primal", "dual"):
         np.testing.assert_allclose(hist[key], ref[key], rtol=REL_ADMM, atol=1e-9, err_msg=key)
 
@@ -178,19 +187,22 @@ def test_admm_solutions_match_oracle_after_gauge(lib):
     J, Z, Y = cal.solutions()
     ref = O.admm(rounded(prob), 5)
     for a in range(prob["A"]):
-        assert np.abs(J[a] - ref["J"][a]).max() < 2e-3
-    assert np.abs(Z[0] - ref["Z"][0]).max() < 2e-3
+        assert np.abs(J[a] - ref["J"][a]).max() < 5e-4
+    assert np.abs(Z[0] - ref["Z"][0]).max() < 5e-3
 
 
-def test_full_size_lofar_interval_sample(lib):
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_full_size_lofar_interval_sample(lib, form):
     """The full LOFAR-shaped batch (62 stations, 5 directions, 32 subbands, 10 intervals,
     10 samples) in the benchmark's launch configuration; the oracle recomputes interval 0."""
     prob = make_problem("lofar_n62_k5")
     n_iter = 2
-    cal = calibrator(lib, prob)
+    cal = calibrator(lib, prob, formulation=FORMS[form])
     hist = cal.iterate(n_iter)
     L, g = cal.agent_objective()
-    ref = O.admm(rounded(prob), n_iter, intervals=[0])
+    if "lofar" not in _ORACLE_CACHE:  # the oracle's interval 0 serves both formulations
+        _ORACLE_CACHE["lofar"] = O.admm(rounded(prob), n_iter, intervals=[0])
+    ref = _ORACLE_CACHE["lofar"]
     P = prob["P"]
     assert float(np.sum(L[:P])) == pytest.approx(sum(ref["L"][a] for a in range(P)), rel=REL_ADMM)
     assert float(np.sum(g[:P])) == pytest.approx(sum(ref["g"][a] for a in range(P)), rel=REL_ADMM)
