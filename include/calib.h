@@ -177,6 +177,16 @@ int calib_profile_enable(calib_ctx* ctx, int on);
 int calib_profile_read(calib_ctx* ctx, int cap, const char** names, double* total_ms,
                        long long* launches, double* bytes_per_launch);
 
+/* Autotuner: time the sweeps of one LM step (n_cg Hessian passes and one trial pass) on the
+ * loaded data for 1, 2, 4, ... diagonals per CTA and the whole agent per CTA, and keep the
+ * fastest (the CTA-to-work split of every sweep launch). calib_admm_iter runs it by itself
+ * before its first iteration when calib_options.chunk_diagonals is 0; the choice is cached per
+ * problem shape for the process. This call re-measures. Outputs (host, any may be NULL): the
+ * chosen value, up to cap candidates and their milliseconds per LM step, and the candidate count.
+ * The iteration state (J, Z, Y) is not changed. */
+int calib_autotune(calib_ctx* ctx, int* chunk_diagonals, int cap, int* candidates,
+                   double* ms_per_lm_step, int* n_candidates);
+
 /* Number of kernels this context has launched since creation (all kinds). */
 long long calib_launch_count(calib_ctx* ctx);
 

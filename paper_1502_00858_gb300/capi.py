@@ -23,6 +23,7 @@ EXPORTED = [
     "calib_reset", "calib_set_initial", "calib_set_consensus", "calib_admm_iter", "calib_get_solutions",
     "calib_get_agent_objective", "calib_eval", "calib_hessvec", "calib_sync", "calib_profile_enable",
     "calib_profile_read", "calib_launch_count", "calib_last_error", "calib_destroy", "calib_eval_noalloc",
+    "calib_autotune",
 ]
 
 
@@ -76,6 +77,7 @@ def load(path: str = LIB_PATH):
         "calib_last_error": (C.c_char_p, []),
         "calib_destroy": (None, [vp]),
         "calib_eval_noalloc": (i, [i, i, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
+        "calib_autotune": (i, [vp, vp, i, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -252,3 +254,14 @@ def calib_eval_noalloc(n_agents, n_stations, n_baselines, n_dirs, n_samples, pq,
     _check(load().calib_eval_noalloc(int(n_agents), int(n_stations), int(n_baselines), int(n_dirs),
                                      int(n_samples), *ptrs, rh.ctypes.data, _ptr(L)[0], _ptr(g)[0],
                                      _ptr(grad)[0], cuda_stream))
+
+
+def calib_autotune(ctx):
+    """Re-measure the sweep split; returns (chosen diagonals per CTA, {candidate: ms per LM step})."""
+    cap = 64
+    chosen = C.c_int()
+    cand = np.zeros(cap, dtype=np.int32)
+    ms = np.zeros(cap)
+    n = C.c_int()
+    _check(load().calib_autotune(ctx, C.byref(chosen), cap, cand.ctypes.data, ms.ctypes.data, C.byref(n)))
+    return chosen.value, {int(cand[i]): float(ms[i]) for i in range(n.value)}

@@ -54,6 +54,8 @@ struct calib_ctx {
     int dev = 0;
     int N = 0, B = 0, K = 0, P = 0, M = 0, I = 0, A = 0, D = 0;
     int n_lm = 10, n_cg = 4, chunk_diags = 1, n_chunks = 1, slots_max = 4;
+    bool tune_pending = false;     // chunk size chosen by the autotuner at the first iteration
+    std::vector<std::pair<int, double>> tune_log;  // (diagonals per CTA, ms per LM step)
     int TT_res = 1, TT_hv = 1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -507,6 +509,90 @@ int ensure_stats(calib_ctx* c, int n) {
 
 bool valid_kind(int k) { return k == 0 || k == 1; }
 
+// Shape class of a tuning result: the timing depends on these alone.
+struct TuneKey {
+    int N, K, A, D, form, n_cg;
+    long long work;  // total slot-samples (direct form) or slots (statistics)
+    bool operator<(const TuneKey& o) const {
+        return std::tie(N, K, A, D, form, n_cg, work) < std::tie(o.N, o.K, o.A, o.D, o.form, o.n_cg, o.work);
+    }
+};
+std::map<TuneKey, int>& tune_cache() {
+    static std::map<TuneKey, int> m;
+    return m;
+}
+
+// Time the sweeps of one LM step (n_cg Hessian passes + one trial pass, without the fused LM
+// work) for candidate numbers of diagonals per CTA and keep the fastest. Runs on the context's
+// data; leaves the iteration state untouched (sweep outputs are scratch).
+int autotune(calib_ctx* c) {
+    long long work = 0;
+    for (const DiagDesc& d : c->desc_h) work += (long long)d.n * (c->formulation == 0 ? 1 : 1);
+    for (int a = 0; a < c->A && c->formulation == 1; ++a) work += (long long)c->T[a];
+    const TuneKey key{c->N, c->K, c->A, c->D, c->formulation, c->n_cg, work};
+    auto hit = tune_cache().find(key);
+    c->tune_log.clear();
+    if (hit != tune_cache().end()) {
+        c->chunk_diags = hit->second;
+        c->n_chunks = (c->D + c->chunk_diags - 1) / c->chunk_diags;
+        c->tune_pending = false;
+        clear_graphs(c);
+        return CALIB_OK;
+    }
+    std::vector<int> cands;
+    for (int cd = 1; cd <= c->D; cd *= 2) cands.push_back(cd);
+    if (cands.back() != c->D) cands.push_back(c->D);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int best_cd = c->chunk_diags;
+    const int reps = 3;
+    for (int cd : cands) {
+        c->chunk_diags = cd;
+        c->n_chunks = (c->D + cd - 1) / cd;
+        auto one_step = [&]() -> cudaError_t {
+            cudaError_t err = cudaSuccess;
+            for (int k = 0; k < c->n_cg && err == cudaSuccess; ++k) {
+                if (c->formulation == 0) {
+                    SSArgs sa = ss_args(c, c->J, c->p);
+                    err = launch_ss_sweep(sa, true, c->stream);
+                } else {
+                    err = launch_sweep(sweep_args(c, SWEEP_HESSVEC, c->J, c->p), SWEEP_HESSVEC, c->stream);
+                }
+            }
+            if (err != cudaSuccess) return err;
+            if (c->formulation == 0) {
+                SSArgs sa = ss_args(c, c->J, c->x);
+                return launch_ss_sweep(sa, false, c->stream);
+            }
+            return launch_sweep(sweep_args(c, SWEEP_TRIAL, c->J, c->x), SWEEP_TRIAL, c->stream);
+        };
+        CK(one_step());  // warm
+        CK(cudaEventRecord(e0, c->stream));
+        for (int r = 0; r < reps; ++r) CK(one_step());
+        CK(cudaEventRecord(e1, c->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        const double per = ms / reps;
+        c->launches += (long long)(reps + 1) * (c->n_cg + 1);
+        c->tune_log.emplace_back(cd, per);
+        if (per < best) {
+            best = per;
+            best_cd = cd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->chunk_diags = best_cd;
+    c->n_chunks = (c->D + best_cd - 1) / best_cd;
+    c->tune_pending = false;
+    tune_cache()[key] = best_cd;
+    clear_graphs(c);
+    return check_status(c);
+}
+
 }  // namespace
 
 void calib::set_last_error(const std::string& msg) { g_err = msg; }
@@ -595,6 +681,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     if (opt.chunk_diagonals > 0) {
         c->chunk_diags = std::min(opt.chunk_diagonals, c->D);
     } else {
+        c->tune_pending = true;  // provisional choice below until calib_autotune runs
         const int want = std::max(1, std::min(c->D, (1216 + A - 1) / A));
         c->chunk_diags = (c->D + want - 1) / want;
     }
@@ -621,9 +708,10 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
                        &c->evJ, &c->evE, &c->evOut})
         okm = okm && dalloc(pp, vec) == cudaSuccess;
     okm = okm && dalloc(&c->Gm, (size_t)A * K * N * 4) == cudaSuccess;
-    okm = okm && dalloc(&c->part, (size_t)A * c->n_chunks * K * N * 8) == cudaSuccess;
-    okm = okm && dalloc(&c->part_cost, (size_t)A * c->n_chunks) == cudaSuccess;
-    okm = okm && dalloc(&c->part_dcost, (size_t)A * c->n_chunks) == cudaSuccess;
+    // partials sized for one diagonal per CTA, the largest chunk count the autotuner may pick
+    okm = okm && dalloc(&c->part, (size_t)A * c->D * K * N * 8) == cudaSuccess;
+    okm = okm && dalloc(&c->part_cost, (size_t)A * c->D) == cudaSuccess;
+    okm = okm && dalloc(&c->part_dcost, (size_t)A * c->D) == cudaSuccess;
     const size_t zs = (size_t)c->I * K * M * N * 8;
     okm = okm && dalloc(&c->Z, zs) == cudaSuccess && dalloc(&c->Zprev, zs) == cudaSuccess;
     okm = okm && dalloc(&c->basis_d, (size_t)P * M) == cudaSuccess && dalloc(&c->Pinv_d, (size_t)M * M) == cudaSuccess;
@@ -847,6 +935,11 @@ int calib_admm_iter(calib_ctx* c, int n_iters, calib_stats* hist) {
         c->launches += 1;
         c->ss_dirty = false;
     }
+    if (c->tune_pending) {
+        rc = autotune(c);
+        if (rc) return rc;
+        CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    }
     const auto key = std::make_tuple(n_iters, c->need_eval ? 1 : 0, c->cold ? 1 : 0, c->profiling ? 1 : 0);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
@@ -995,6 +1088,28 @@ int calib_profile_read(calib_ctx* c, int cap, const char** names, double* total_
 }
 
 long long calib_launch_count(calib_ctx* c) { return c ? c->launches : 0; }
+
+int calib_autotune(calib_ctx* c, int* chunk_diagonals, int cap, int* cand, double* ms_per_lm_step, int* n_cand) {
+    if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
+    if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "set visibilities and coherencies first");
+    if (c->formulation == 0 && c->ss_dirty) {
+        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->T_d, c->A, c->D, c->K, c->stream));
+        c->launches += 1;
+        c->ss_dirty = false;
+    }
+    CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
+    tune_cache().clear();
+    const int rc = autotune(c);
+    if (rc) return rc;
+    if (chunk_diagonals) *chunk_diagonals = c->chunk_diags;
+    const int n = (int)c->tune_log.size();
+    for (int i = 0; i < n && i < cap; ++i) {
+        if (cand) cand[i] = c->tune_log[i].first;
+        if (ms_per_lm_step) ms_per_lm_step[i] = c->tune_log[i].second;
+    }
+    if (n_cand) *n_cand = n;
+    return CALIB_OK;
+}
 
 const char* calib_last_error(void) { return g_err.c_str(); }
 
