@@ -187,6 +187,40 @@ int calib_profile_read(calib_ctx* ctx, int cap, const char** names, double* tota
 int calib_autotune(calib_ctx* ctx, int* chunk_diagonals, int cap, int* candidates,
                    double* ms_per_lm_step, int* n_candidates);
 
+/* ---- Learned warm start (the paper starts a calibration from the previous time slot's solution,
+ * Section 3, initialisation; a small network refines that start).
+ * Network: rows of 17 inputs (J_prev of one station and direction as 8 reals (re, im of the 2x2
+ * row-major entries), (B_f Z_prev) likewise, normalised frequency (f - f_min)/(f_max - f_min)),
+ * `depth` ReLU layers of `width`, 8 outputs y; J_init = J_prev + y. bfloat16 weights and biases
+ * (copies of float32 master weights), float32 accumulation; AdamW on the mean squared error.
+ * Weights are a flat float32 array [W_1 (width x 17), b_1, ..., W_last (8 x width), b_last],
+ * row-major; calib_mlp_num_params gives its length. A network has its own stream (cuda_stream
+ * NULL = its own) and is not thread-safe. The paper has no network: this is the warm-start
+ * pattern of the build, judged by the ADMM's own objective (calib_warm_start). */
+typedef struct calib_mlp calib_mlp;
+int calib_mlp_create(calib_mlp** out, int n_in, int width, int depth, int n_out, void* cuda_stream);
+long long calib_mlp_num_params(calib_mlp* mlp);
+int calib_mlp_set_weights(calib_mlp* mlp, const float* w, int ptr_kind);   /* resets the optimiser */
+int calib_mlp_get_weights(calib_mlp* mlp, float* w, int ptr_kind);
+/* y [rows][8] for rows X [rows][17] (float32). */
+int calib_mlp_forward(calib_mlp* mlp, const float* X, float* Y, int rows, int ptr_kind);
+/* Loss mean_r ||X[r,0:8] + y_r - T_r||^2 and its gradient w.r.t. the float32 weights (flat layout);
+ * grad and loss may be NULL. */
+int calib_mlp_grad(calib_mlp* mlp, const float* X, const float* T, int rows, float* grad, double* loss, int ptr_kind);
+/* One AdamW step (beta 0.9/0.999, eps 1e-8, decoupled weight decay) on a batch; loss before the step. */
+int calib_mlp_train_step(calib_mlp* mlp, const float* X, const float* T, int rows, float lr, float weight_decay,
+                         double* loss, int ptr_kind);
+void calib_mlp_destroy(calib_mlp* mlp);
+/* Feature rows [A*K*N][17] of the context's current state (J and B_f Z after the last iteration,
+ * normalised frequency), rows ordered (agent, direction, station): the network's inputs for the
+ * following interval. */
+int calib_get_features(calib_ctx* ctx, float* X, int ptr_kind);
+/* Warm start of the next calib_admm_iter from the previous interval's solution J_prev c64 [A][K][N][2][2]
+ * and consensus Z_prev c128 [I][K][M][N][2][2]: Z = Z_prev, Y = 0 (warm: no gauge projection), and per
+ * agent J = J_prev + network(J_prev, B_f Z_prev, f) where that gives the lower L_i, else J = J_prev
+ * (mlp NULL: always J_prev). chose [A] (may be NULL) receives 1 where the network's start was kept. */
+int calib_warm_start(calib_ctx* ctx, calib_mlp* mlp, const void* J_prev, const void* Z_prev, int* chose, int ptr_kind);
+
 /* Number of kernels this context has launched since creation (all kinds). */
 long long calib_launch_count(calib_ctx* ctx);
 

@@ -23,7 +23,9 @@ EXPORTED = [
     "calib_reset", "calib_set_initial", "calib_set_consensus", "calib_admm_iter", "calib_get_solutions",
     "calib_get_agent_objective", "calib_eval", "calib_hessvec", "calib_sync", "calib_profile_enable",
     "calib_profile_read", "calib_launch_count", "calib_last_error", "calib_destroy", "calib_eval_noalloc",
-    "calib_autotune",
+    "calib_autotune", "calib_mlp_create", "calib_mlp_num_params", "calib_mlp_set_weights", "calib_mlp_get_weights",
+    "calib_mlp_forward", "calib_mlp_grad", "calib_mlp_train_step", "calib_mlp_destroy", "calib_get_features",
+    "calib_warm_start",
 ]
 
 
@@ -78,6 +80,16 @@ def load(path: str = LIB_PATH):
         "calib_destroy": (None, [vp]),
         "calib_eval_noalloc": (i, [i, i, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
         "calib_autotune": (i, [vp, vp, i, vp, vp, vp]),
+        "calib_mlp_create": (i, [C.POINTER(vp), i, i, i, i, vp]),
+        "calib_mlp_num_params": (C.c_longlong, [vp]),
+        "calib_mlp_set_weights": (i, [vp, vp, i]),
+        "calib_mlp_get_weights": (i, [vp, vp, i]),
+        "calib_mlp_forward": (i, [vp, vp, vp, i, i]),
+        "calib_mlp_grad": (i, [vp, vp, vp, i, vp, vp, i]),
+        "calib_mlp_train_step": (i, [vp, vp, vp, i, C.c_float, C.c_float, vp, i]),
+        "calib_mlp_destroy": (None, [vp]),
+        "calib_get_features": (i, [vp, vp, i]),
+        "calib_warm_start": (i, [vp, vp, vp, vp, vp, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -265,3 +277,69 @@ def calib_autotune(ctx):
     n = C.c_int()
     _check(load().calib_autotune(ctx, C.byref(chosen), cap, cand.ctypes.data, ms.ctypes.data, C.byref(n)))
     return chosen.value, {int(cand[i]): float(ms[i]) for i in range(n.value)}
+
+
+# ----------------------------------------------------------------------------- warm-start network
+
+def calib_mlp_create(width=256, depth=3, cuda_stream=None):
+    h = C.c_void_p()
+    _check(load().calib_mlp_create(C.byref(h), 17, int(width), int(depth), 8, cuda_stream))
+    return h
+
+
+def calib_mlp_num_params(h) -> int:
+    return int(load().calib_mlp_num_params(h))
+
+
+def calib_mlp_set_weights(h, w):
+    p, k, keep = _ptr(w, np.float32)
+    _check(load().calib_mlp_set_weights(h, p, k))
+
+
+def calib_mlp_get_weights(h, out=None):
+    if out is None:
+        out = np.zeros(calib_mlp_num_params(h), dtype=np.float32)
+    p, k, _ = _ptr(out)
+    _check(load().calib_mlp_get_weights(h, p, k))
+    return out
+
+
+def calib_mlp_forward(h, X, Y):
+    px, kx, a = _ptr(X, np.float32)
+    py, ky, _ = _ptr(Y)
+    _check(load().calib_mlp_forward(h, px, py, int(X.shape[0]), _kind(kx, ky)))
+    return Y
+
+
+def calib_mlp_grad(h, X, T, grad=None, loss=None):
+    px, kx, a = _ptr(X, np.float32)
+    pt, kt, b = _ptr(T, np.float32)
+    pg, _, _ = _ptr(grad)
+    pl, _, _ = _ptr(loss)
+    _check(load().calib_mlp_grad(h, px, pt, int(X.shape[0]), pg, pl, _kind(kx, kt)))
+
+
+def calib_mlp_train_step(h, X, T, lr, weight_decay, loss=None):
+    px, kx, a = _ptr(X, np.float32)
+    pt, kt, b = _ptr(T, np.float32)
+    pl, _, _ = _ptr(loss)
+    _check(load().calib_mlp_train_step(h, px, pt, int(X.shape[0]), C.c_float(lr), C.c_float(weight_decay), pl,
+                                       _kind(kx, kt)))
+
+
+def calib_mlp_destroy(h):
+    if h:
+        load().calib_mlp_destroy(h)
+
+
+def calib_get_features(ctx, X):
+    p, k, _ = _ptr(X)
+    _check(load().calib_get_features(ctx, p, k))
+    return X
+
+
+def calib_warm_start(ctx, mlp, J_prev, Z_prev, chose=None):
+    pj, kj, a = _ptr(J_prev, np.complex64)
+    pz, kz, b = _ptr(Z_prev, np.complex128)
+    pc, _, _ = _ptr(chose)
+    _check(load().calib_warm_start(ctx, mlp, pj, pz, pc, _kind(kj, kz)))

@@ -25,6 +25,8 @@
 
 #include <string>
 
+typedef struct calib_mlp calib_mlp;
+
 namespace calib {
 
 constexpr int MAX_N = 256;
@@ -174,6 +176,14 @@ cudaError_t prepare_ss_kernels();
 cudaError_t prepare_sweep_kernels();
 cudaError_t prepare_lm_kernels();
 cudaError_t prepare_data_kernels();
+
+// Warm-start network pieces (mlp.cu) used by calib_warm_start.
+cudaError_t mlp_warm_rows(calib_mlp* h, const float* J_prev, const float* BZ, const double* xf, int K, int N, int A,
+                          float* J_mlp, cudaStream_t s);
+cudaError_t mlp_warm_select(const float* J_mlp, const float* J_prev, const double* L_mlp, const double* L_prev, int KN8,
+                            int A, float* J_out, int* chose, cudaStream_t s);
+cudaError_t launch_ws_features(const float* J, const float* BZ, const double* xf, int K, int N, long long rows, float* X,
+                               cudaStream_t s);
 
 // Record the message returned by calib_last_error() on this thread (capi.cu).
 void set_last_error(const std::string& msg);

@@ -106,6 +106,9 @@ struct calib_ctx {
     double* evG = nullptr;
     void* staging = nullptr;
     size_t staging_bytes = 0;
+    float *ws_prev = nullptr, *ws_mlp = nullptr;   // warm start: previous J, network J
+    double *ws_L = nullptr, *xf_d = nullptr;         // [2A] L at both starts; [A] normalised frequency
+    int* ws_chose = nullptr;
 
     bool data_set = false, coh_set = false;
     bool cold = true, need_eval = true;
@@ -1089,6 +1092,81 @@ int calib_profile_read(calib_ctx* c, int cap, const char** names, double* total_
 
 long long calib_launch_count(calib_ctx* c) { return c ? c->launches : 0; }
 
+int calib_get_features(calib_ctx* c, float* X, int ptr_kind) {
+    if (!c || !X) return fail(CALIB_EINVAL, "ctx and X are required");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    const size_t rows = (size_t)c->A * c->K * c->N;
+    if (!c->xf_d) {
+        if (dalloc(&c->xf_d, (size_t)c->A) != cudaSuccess) return fail(CALIB_ENOMEM, "frequency buffer");
+        std::vector<double> xf(c->A);
+        const double fmin = *std::min_element(c->freqs.begin(), c->freqs.end());
+        const double fmax = *std::max_element(c->freqs.begin(), c->freqs.end());
+        for (int a = 0; a < c->A; ++a) xf[a] = fmax > fmin ? (c->freqs[a % c->P] - fmin) / (fmax - fmin) : 0.0;
+        CK(cudaMemcpy(c->xf_d, xf.data(), xf.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    float* dst = X;
+    if (ptr_kind == 0) {
+        int rc = ensure_staging(c, rows * 17 * sizeof(float));
+        if (rc) return rc;
+        dst = static_cast<float*>(c->staging);
+    }
+    CK(launch_ws_features(c->J, c->BZ, c->xf_d, c->K, c->N, (long long)rows, dst, c->stream));
+    c->launches += 1;
+    if (ptr_kind == 0) {
+        CK(cudaMemcpyAsync(X, dst, rows * 17 * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return CALIB_OK;
+}
+
+int calib_warm_start(calib_ctx* c, calib_mlp* mlp, const void* J_prev, const void* Z_prev, int* chose, int ptr_kind) {
+    if (!c || !J_prev || !Z_prev) return fail(CALIB_EINVAL, "ctx, J_prev and Z_prev are required");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "set visibilities and coherencies first");
+    const size_t vec = (size_t)c->A * c->K * c->N * 8;
+    if (!c->ws_prev) {
+        bool ok = dalloc(&c->ws_prev, vec) == cudaSuccess && dalloc(&c->ws_mlp, vec) == cudaSuccess &&
+                  dalloc(&c->ws_L, 2 * (size_t)c->A) == cudaSuccess && dalloc(&c->ws_chose, (size_t)c->A) == cudaSuccess;
+        if (!c->xf_d) ok = ok && dalloc(&c->xf_d, (size_t)c->A) == cudaSuccess;
+        if (!ok) return fail(CALIB_ENOMEM, "warm-start buffers");
+        std::vector<double> xf(c->A);
+        const double fmin = *std::min_element(c->freqs.begin(), c->freqs.end());
+        const double fmax = *std::max_element(c->freqs.begin(), c->freqs.end());
+        for (int a = 0; a < c->A; ++a) xf[a] = fmax > fmin ? (c->freqs[a % c->P] - fmin) / (fmax - fmin) : 0.0;
+        CK(cudaMemcpy(c->xf_d, xf.data(), xf.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    // consensus from the previous interval (warm: no first-iteration projection), Y = 0
+    int rc = calib_set_consensus(c, Z_prev, nullptr, ptr_kind);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->ws_prev, J_prev, vec * sizeof(float),
+                       ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    if (mlp) {
+        CK(mlp_warm_rows(mlp, c->ws_prev, c->BZ, c->xf_d, c->K, c->N, c->A, c->ws_mlp, c->stream));
+        LMArgs la = lm_args(c);
+        const float* starts[2] = {c->ws_mlp, c->ws_prev};
+        for (int i = 0; i < 2; ++i) {
+            CK(launch_sweep(sweep_args(c, SWEEP_RESIDUAL, starts[i], nullptr), SWEEP_RESIDUAL, c->stream));
+            la.Jt = const_cast<float*>(starts[i]);
+            CK(launch_eval_output(la, c->evOut, c->ws_L + (size_t)i * c->A, nullptr, c->stream));
+        }
+        CK(mlp_warm_select(c->ws_mlp, c->ws_prev, c->ws_L, c->ws_L + c->A, c->K * c->N * 8, c->A, c->J, c->ws_chose,
+                           c->stream));
+        c->launches += 7;
+        if (chose) CK(cudaMemcpyAsync(chose, c->ws_chose, (size_t)c->A * sizeof(int),
+                                      ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    } else {
+        CK(cudaMemcpyAsync(c->J, c->ws_prev, vec * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        if (chose) {
+            if (ptr_kind == 1) CK(cudaMemsetAsync(chose, 0, (size_t)c->A * sizeof(int), c->stream));
+            else std::fill(chose, chose + c->A, 0);
+        }
+    }
+    c->need_eval = true;
+    c->cold = false;
+    if (ptr_kind == 0) CK(cudaStreamSynchronize(c->stream));
+    return CALIB_OK;
+}
+
 int calib_autotune(calib_ctx* c, int* chunk_diagonals, int cap, int* cand, double* ms_per_lm_step, int* n_cand) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "set visibilities and coherencies first");
@@ -1124,7 +1202,8 @@ void calib_destroy(calib_ctx* c) {
                     (void*)c->Z, (void*)c->Zprev, (void*)c->basis_d, (void*)c->Pinv_d, (void*)c->freqs_d,
                     (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->dual2, (void*)c->stats, (void*)c->iter_counter,
                     (void*)c->status, (void*)c->arrive, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
-                    (void*)c->coh_off_d, c->staging})
+                    (void*)c->coh_off_d, c->staging, (void*)c->ws_prev, (void*)c->ws_mlp, (void*)c->ws_L,
+                    (void*)c->xf_d, (void*)c->ws_chose})
         if (p) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

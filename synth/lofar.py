@@ -88,6 +88,10 @@ SPECS: dict[str, ProblemSpec] = {
                                   sky_kind="clusters", basis_kind="bernstein", degree=3,
                                   rho=10.0, snr=10.0, n_admm=50, jones_kind="smooth_deg3",
                                   flag_max=0.15, seed=2),
+    # learned warm start: 62 stations, 5 directions, 64 subbands, drifting consecutive intervals.
+    "warm_n62_k5": ProblemSpec("warm_n62_k5", N=62, K=5, P=64, I=3, T=10, n_src=20,
+                               sky_kind="clusters", basis_kind="bernstein", degree=3,
+                               rho=10.0, snr=10.0, n_admm=30, jones_kind="smooth_deg3", seed=4),
     # adjoint check size: 16 stations, 3 directions, 8 frequencies, 2 samples.
     "adjoint_n16_k3": ProblemSpec("adjoint_n16_k3", N=16, K=3, P=8, I=1, T=2, n_src=5,
                                   sky_kind="clusters", basis_kind="bernstein", degree=3,
@@ -222,7 +226,7 @@ def simulate_visibilities(Jt: np.ndarray, C: np.ndarray, pq: np.ndarray) -> np.n
 def make_problem(spec: ProblemSpec | str, seed: int | None = None, *, I: int | None = None,
                  P: int | None = None, N: int | None = None, K: int | None = None,
                  T: int | Sequence[int] | None = None, flag_max: float | None = None,
-                 noise: bool = True) -> dict:
+                 noise: bool = True, dtype=complex) -> dict:
     """Build a seeded problem. Keyword overrides shrink or reshape a named spec."""
     if isinstance(spec, str):
         spec = SPECS[spec]
@@ -262,21 +266,23 @@ def make_problem(spec: ProblemSpec | str, seed: int | None = None, *, I: int | N
         flags = (rng.uniform(0, 1, (A, B)) < frac[:, None]).astype(np.uint8)
 
     Cs, Vs = [], []
+    sig, cnt = 0.0, 0
     for a in range(A):
         iv, fi = divmod(a, P)
         Ta = int(T_agent[a])
         C = simulate_coherencies(uvw[iv, :Ta], sky, float(freqs[fi]), pq)
-        Cs.append(C)
-        Vs.append(simulate_visibilities(J_true[a], C, pq))
+        V = simulate_visibilities(J_true[a], C, pq)
+        sig += float(np.sum(np.abs(V[flags[a] == 0]) ** 2))
+        cnt += int(np.sum(flags[a] == 0)) * Ta * 4
+        Cs.append(C.astype(dtype, copy=False))
+        Vs.append(V.astype(dtype, copy=False))
     # Noise: total noise power = total signal power / SNR over all unflagged data
     # (equal variance in real and imaginary parts, Section 2 and Section 4).
-    sig = sum(float(np.sum(np.abs(V[flags[a] == 0]) ** 2)) for a, V in enumerate(Vs))
-    cnt = sum(int(np.sum(flags[a] == 0)) * V.shape[1] * 4 for a, V in enumerate(Vs))
     sigma = math.sqrt(sig / cnt / (2.0 * spec.snr)) if (noise and cnt) else 0.0
     if sigma > 0:
         for a in range(A):
             shape = Vs[a].shape
-            Vs[a] = Vs[a] + sigma * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))
+            Vs[a] = Vs[a] + (sigma * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))).astype(dtype, copy=False)
     return dict(spec=spec, N=N, K=K, P=P, I=I, M=spec.M, B=B, A=A, pq=pq, freqs=freqs, basis=basis,
                 rho=rho, T=T_agent, flags=flags, uvw=uvw, sky=sky, f0=F0_HZ, J_true=J_true,
                 V=Vs, C=Cs, sigma=sigma, n_admm=spec.n_admm)
