@@ -21,7 +21,8 @@
 namespace calib {
 namespace {
 
-constexpr int NST = 3;
+constexpr int NST = 2;   // one stage = one whole diagonal; one stage of prefetch hides the bulk-copy latency
+constexpr int BAR_BYTES = 64;  // barrier area, keeps the rows below 16-byte aligned
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -89,10 +90,13 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
 
     unsigned char* stage = smem;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NST * stage_bytes);
-    float2* Js = reinterpret_cast<float2*>(bar + NST);  // [K][N][4]
+    float2* Js = reinterpret_cast<float2*>(smem + NST * stage_bytes + BAR_BYTES);  // [K][N][4]
     float2* Es = Js + KN4;                                // [K][N][4] eta or x
-    float2* acc = Es + KN4;                               // [K][N][4]
-    double* red = reinterpret_cast<double*>(acc + KN4);   // [64]
+    float2* acc = Es + KN4;                               // [K][N][4] first-station sums
+    // Hessian pass: second-station sums in their own array, so the two scatter phases of a
+    // diagonal need no barrier between them (the next diagonal's stage barrier orders them).
+    float2* accs = HV ? acc + KN4 : acc;
+    double* red = reinterpret_cast<double*>(accs + KN4);  // [64]
 
     const float2* Jg = reinterpret_cast<const float2*>(a.J) + (size_t)agent * KN4;
     const float2* Eg = reinterpret_cast<const float2*>(a.eta) + (size_t)agent * KN4;
@@ -100,6 +104,7 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
         Js[i] = Jg[i];
         Es[i] = Eg[i];
         acc[i] = make_float2(0.f, 0.f);
+        if (HV) accs[i] = make_float2(0.f, 0.f);
     }
     const int d0 = 1 + chunk * a.chunk_diags;
     const int d1 = min(D, d0 + a.chunk_diags - 1);
@@ -158,17 +163,22 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
 #pragma unroll
             for (int l = 0; l < KB; ++l) {
                 if (l < K) {
-                    const float2* jf = Js + (l * N + first) * 4;
-                    const float2* js = Js + (l * N + second) * 4;
-                    const float2* ef = Es + (l * N + first) * 4;
-                    const float2* es = Es + (l * N + second) * 4;
-                    const float2 jfs = f2add(cmul_cb(jf[rr * 2 + 0], js[cc * 2 + 0]), cmul_cb(jf[rr * 2 + 1], js[cc * 2 + 1]));
-                    const float2 efs = f2add(cmul_cb(ef[rr * 2 + 0], js[cc * 2 + 0]), cmul_cb(ef[rr * 2 + 1], js[cc * 2 + 1]));
-                    const float2 jfe = f2add(cmul_cb(jf[rr * 2 + 0], es[cc * 2 + 0]), cmul_cb(jf[rr * 2 + 1], es[cc * 2 + 1]));
+                    // row rr of J_f / eta_f and row cc of J_s / eta_s, one 16-byte load each
+                    const float4 jf = *reinterpret_cast<const float4*>(Js + (l * N + first) * 4 + rr * 2);
+                    const float4 js = *reinterpret_cast<const float4*>(Js + (l * N + second) * 4 + cc * 2);
+                    const float4 ef = *reinterpret_cast<const float4*>(Es + (l * N + first) * 4 + rr * 2);
+                    const float4 es = *reinterpret_cast<const float4*>(Es + (l * N + second) * 4 + cc * 2);
+                    const float2 jf0 = make_float2(jf.x, jf.y), jf1 = make_float2(jf.z, jf.w);
+                    const float2 js0 = make_float2(js.x, js.y), js1 = make_float2(js.z, js.w);
+                    const float2 ef0 = make_float2(ef.x, ef.y), ef1 = make_float2(ef.z, ef.w);
+                    const float2 es0 = make_float2(es.x, es.y), es1 = make_float2(es.z, es.w);
+                    const float2 jfs = f2add(cmul_cb(jf0, js0), cmul_cb(jf1, js1));
+                    const float2 efs = f2add(cmul_cb(ef0, js0), cmul_cb(ef1, js1));
+                    const float2 jfe = f2add(cmul_cb(jf0, es0), cmul_cb(jf1, es1));
                     if (HV) {
                         Pa[l] = f2add(efs, jfe);
                     } else {
-                        const float2 efe = f2add(cmul_cb(ef[rr * 2 + 0], es[cc * 2 + 0]), cmul_cb(ef[rr * 2 + 1], es[cc * 2 + 1]));
+                        const float2 efe = f2add(cmul_cb(ef0, es0), cmul_cb(ef1, es1));
                         Pa[l] = jfs;
                         Pb[l] = f2add(f2add(efs, jfe), efe);
                     }
@@ -178,6 +188,14 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
                 }
             }
             float dcf = 0.f;
+            // small exact K: the packed S of the slot in registers, each entry loaded once
+            constexpr bool SREG = EXACT && KB <= 6;
+            constexpr int KKR = SREG ? KB * (KB + 1) / 2 : 1;
+            float2 Sr[KKR];
+            if (SREG) {
+#pragma unroll
+                for (int i = 0; i < KKR; ++i) Sr[i] = Ss[i];
+            }
 #pragma unroll
             for (int k = 0; k < KB; ++k) {
                 if (k < K) {
@@ -187,7 +205,8 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
                         if (l < K) {
                             // S_kl from the packed upper triangle; S_kl = conj(S_lk) below the diagonal
                             const int lo = k < l ? k : l, hi = k < l ? l : k;
-                            float2 skl = Ss[lo * K - lo * (lo - 1) / 2 + (hi - lo)];
+                            const int si = lo * K - lo * (lo - 1) / 2 + (hi - lo);
+                            float2 skl = SREG ? Sr[si < KKR ? si : 0] : Ss[si];
                             if (k > l) skl.y = -skl.y;
                             cmac(sa, skl, Pa[l]);
                             if (!HV) cmac(sb, skl, Pb[l]);
@@ -226,7 +245,7 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
                 }
             }
         }
-        __syncthreads();
+        if (!HV) __syncthreads();
         // Phase 2: second station receives -X_k^H J'_f.
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
@@ -242,7 +261,7 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
                         j1 = f2add(j1, xf[1 * 2 + cc]);
                     }
                     const float2 v = f2add(cmul_ca(w0, j0), cmul_ca(w1, j1));
-                    float2* dd = acc + (k * N + second) * 4 + e;
+                    float2* dd = accs + (k * N + second) * 4 + e;
                     *dd = f2sub(*dd, v);
                 }
             }
@@ -250,7 +269,7 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
     }
     __syncthreads();
     float2* out = reinterpret_cast<float2*>(a.part) + ((size_t)agent * a.n_chunks + chunk) * KN4;
-    for (int i = tid; i < KN4; i += nthr) out[i] = acc[i];
+    for (int i = tid; i < KN4; i += nthr) out[i] = HV ? f2add(acc[i], accs[i]) : acc[i];
     if (!HV) {
         for (int o = 16; o > 0; o >>= 1) dcost += __shfl_down_sync(0xffffffffu, dcost, o);
         if (lane == 0) red[tid >> 5] = dcost;
@@ -338,7 +357,7 @@ cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, cudaStream_t s) {
     const int KK = a.K * (a.K + 1) / 2;
     const int per_slot = (hessvec ? 0 : a.K * 32) + KK * 8;
     const int sb = ((a.slots_max * per_slot + 127) / 128) * 128;
-    const size_t smem = (size_t)NST * sb + NST * 8 + (size_t)3 * a.K * a.N * 32 + 64 * 8;
+    const size_t smem = (size_t)NST * sb + BAR_BYTES + (size_t)(hessvec ? 4 : 3) * a.K * a.N * 32 + 64 * 8;
     if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
     const int threads = ((4 * a.slots_max + 31) / 32) * 32;
     return hessvec ? dispatch<true>(a, threads, smem, sb, s) : dispatch<false>(a, threads, smem, sb, s);
