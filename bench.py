@@ -190,7 +190,8 @@ def run_ours(args, world, rank, local):
     cal = Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
                      n_intervals=prob["I"], samples=prob["T"], n_lm=N_LM, n_cg=N_CG,
                      chunk_diagonals=args.chunk_diagonals, cuda_stream=stream.cuda_stream,
-                     formulation=capi.CALIB_FORM_DIRECT if args.formulation == "direct" else capi.CALIB_FORM_STATISTICS)
+                     formulation=capi.CALIB_FORM_DIRECT if args.formulation == "direct" else capi.CALIB_FORM_STATISTICS,
+                     fused_lm=args.fused_lm)
     dev = torch.device("cuda", local)
     vis_d = torch.from_numpy(ul["vis"].view(np.float32)).to(dev)
     uvw_d = torch.from_numpy(np.ascontiguousarray(prob["uvw"])).to(dev)
@@ -313,7 +314,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOAD, "stations": prob["N"], "baselines": prob["B"], "directions": prob["K"],
                        "subbands": prob["P"], "intervals": prob["I"], "samples": 10, "admm_iters": n_admm,
                        "n_lm": N_LM, "n_cg": N_CG, "basis": "Bernstein degree 3", "rho": 10.0,
-                       "formulation": args.formulation,
+                       "formulation": args.formulation, "fused_lm": bool(args.fused_lm),
                        "step": "predict + cold start + 30 C-ADMM iterations",
                        "l2": "inputs larger than L2 (436 MB per residual sweep, 242 MB per Hessian sweep)",
                        "parallelism": f"replica x{world}" if world > 1 else "single GPU",
@@ -338,6 +339,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--chunk-diagonals", type=int, default=0)
     ap.add_argument("--formulation", choices=["statistics", "direct"], default="statistics")
+    ap.add_argument("--fused-lm", action="store_true", help="finish LM/PCG steps inside the sweeps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run one launch of each sweep on the workload and exit (profiler captures)")

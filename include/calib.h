@@ -73,6 +73,8 @@ typedef struct {
     int chunk_diagonals;               /* baseline diagonals per CTA in the sweeps; 0 = automatic */
     void* cuda_stream;                 /* cudaStream_t to run on; NULL = the library creates one */
     int formulation;                   /* CALIB_FORM_STATISTICS (default) or CALIB_FORM_DIRECT */
+    int fused_lm;                      /* statistics form only: 1 = finish each agent's PCG / LM step in the
+                                          last CTA of its sweep; 0 (default) = separate per-agent launches */
 } calib_options;
 
 /* One record per C-ADMM iteration (Section 4 definitions, summed/averaged over all intervals):

@@ -98,13 +98,20 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
     float2* accs = HV ? acc + KN4 : acc;
     double* red = reinterpret_cast<double*>(accs + KN4);  // [64]
 
-    const float2* Jg = reinterpret_cast<const float2*>(a.J) + (size_t)agent * KN4;
-    const float2* Eg = reinterpret_cast<const float2*>(a.eta) + (size_t)agent * KN4;
-    for (int i = tid; i < KN4; i += nthr) {
-        Js[i] = Jg[i];
-        Es[i] = Eg[i];
-        acc[i] = make_float2(0.f, 0.f);
-        if (HV) accs[i] = make_float2(0.f, 0.f);
+    {   // stage J and eta / x, clear the sums: 16-byte accesses (a station block is 32 bytes)
+        const float4* Jg = reinterpret_cast<const float4*>(a.J) + (size_t)agent * KN4 / 2;
+        const float4* Eg = reinterpret_cast<const float4*>(a.eta) + (size_t)agent * KN4 / 2;
+        float4* J4 = reinterpret_cast<float4*>(Js);
+        float4* E4 = reinterpret_cast<float4*>(Es);
+        float4* A4 = reinterpret_cast<float4*>(acc);
+        float4* S4 = reinterpret_cast<float4*>(accs);
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int i = tid; i < KN4 / 2; i += nthr) {
+            J4[i] = __ldg(Jg + i);
+            E4[i] = __ldg(Eg + i);
+            A4[i] = z4;
+            if (HV) S4[i] = z4;
+        }
     }
     const int d0 = 1 + chunk * a.chunk_diags;
     const int d1 = min(D, d0 + a.chunk_diags - 1);
@@ -268,8 +275,15 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
         }
     }
     __syncthreads();
-    float2* out = reinterpret_cast<float2*>(a.part) + ((size_t)agent * a.n_chunks + chunk) * KN4;
-    for (int i = tid; i < KN4; i += nthr) out[i] = HV ? f2add(acc[i], accs[i]) : acc[i];
+    float4* out = reinterpret_cast<float4*>(a.part) + ((size_t)agent * a.n_chunks + chunk) * KN4 / 2;
+    for (int i = tid; i < KN4 / 2; i += nthr) {
+        float4 v = reinterpret_cast<const float4*>(acc)[i];
+        if (HV) {
+            const float4 w = reinterpret_cast<const float4*>(accs)[i];
+            v = make_float4(v.x + w.x, v.y + w.y, v.z + w.z, v.w + w.w);
+        }
+        out[i] = v;
+    }
     if (!HV) {
         for (int o = 16; o > 0; o >>= 1) dcost += __shfl_down_sync(0xffffffffu, dcost, o);
         if (lane == 0) red[tid >> 5] = dcost;
