@@ -35,25 +35,33 @@ N_LM, N_CG = 10, 4
 METRIC = "ADMM vis*dir*iter/s (LOFAR-shaped: N=62, K=5, 32 subbands, 10 intervals x 10 samples)"
 UNIT = "vis*dir*iter/s"
 
-# DRAM traffic per launch of the dominant sweep kernel from one ncu capture; valid only for the
-# kernel source it was taken on (sha256 prefix of sweep.cu), else reported as null.
-NCU_TRAFFIC = {  # profiles/sweep_kernels_lofar_n62_k5.md (dram__bytes_read.sum + dram__bytes_write.sum)
+# DRAM traffic per launch of each sweep kernel from one ncu capture; valid only for the kernel
+# source it was taken on (sha256 prefix of the kernel's .cu file), else reported as null.
+NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum, profiles/*_lofar_n62_k5.md
     ("sweep_hessvec", "8e587c1134b3"): 269.0e6,
     ("sweep_residual", "8e587c1134b3"): 468.0e6,
 }
+KERNEL_SOURCE = {"sweep_residual": "sweep.cu", "sweep_hessvec": "sweep.cu",
+                 "stats_hessvec": "ss.cu", "stats_trial": "ss.cu"}
+# The sufficient-statistics passes do 13-17 real flops per algorithmic byte at K=5, above the FP32
+# ridge (~12 flop/B): their roofline is the FP32 pipe. The direct passes are below it (HBM).
+ALU_BOUND = {"stats_hessvec", "stats_trial"}
+SMS, FP32_LANES_PER_SM = 152, 128
 
 
 def peaks():
+    """(HBM GB/s, FP32 TFLOP/s, source). FP32 peak = SMs x FP32 lanes x 2 flops (FMA) x max SM clock."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             mp = json.load(fh)
-        return float(mp["hbm_gbs"]), "measured"
+        mhz = float(mp.get("sm_max_mhz", 2070.0))
+        return float(mp["hbm_gbs"]), SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, "measured"
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12, "fallback"
 
 
-def sweep_hash() -> str:
-    with open(os.path.join(ROOT, "paper_1502_00858_gb300", "csrc", "sweep.cu"), "rb") as fh:
+def source_hash(kind: str) -> str:
+    with open(os.path.join(ROOT, "paper_1502_00858_gb300", "csrc", KERNEL_SOURCE[kind]), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:12]
 
 
@@ -190,8 +198,7 @@ def run_ours(args, world, rank, local):
     cal = Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
                      n_intervals=prob["I"], samples=prob["T"], n_lm=N_LM, n_cg=N_CG,
                      chunk_diagonals=args.chunk_diagonals, cuda_stream=stream.cuda_stream,
-                     formulation=capi.CALIB_FORM_DIRECT if args.formulation == "direct" else capi.CALIB_FORM_STATISTICS,
-                     fused_lm=args.fused_lm)
+                     formulation=capi.CALIB_FORM_DIRECT if args.formulation == "direct" else capi.CALIB_FORM_STATISTICS)
     dev = torch.device("cuda", local)
     vis_d = torch.from_numpy(ul["vis"].view(np.float32)).to(dev)
     uvw_d = torch.from_numpy(np.ascontiguousarray(prob["uvw"])).to(dev)
@@ -254,18 +261,28 @@ def run_ours(args, world, rank, local):
     capi.calib_profile_enable(cal.ctx, False)
     dom = max(prof, key=lambda k: prof[k]["total_ms"])
     avg_s = prof[dom]["total_ms"] / 1e3 / max(1, prof[dom]["launches"])
-    achieved = prof[dom]["bytes_per_launch"] / avg_s / 1e9
-    peak, peak_kind = peaks()
-    h = sweep_hash()
-    traffic = NCU_TRAFFIC.get((dom, h))
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": dom, "peak_source": peak_kind,
-                "per_kernel": {k: {"avg_us": 1e3 * v["total_ms"] / max(1, v["launches"]),
-                                   "launches": v["launches"],
-                                   "GBps": v["bytes_per_launch"] / (v["total_ms"] / 1e3 / max(1, v["launches"])) / 1e9
-                                   if v["launches"] else None,
-                                   "share_of_step": v["total_ms"] / 1e3 / (dt * 1.0) if dt else None}
-                               for k, v in prof.items()}}
+    hbm_peak, fp32_peak, peak_kind = peaks()
+    hbm_achieved = prof[dom]["bytes_per_launch"] / avg_s / 1e9
+    traffic = NCU_TRAFFIC.get((dom, source_hash(dom)))
+    if dom in ALU_BOUND:
+        achieved = prof[dom]["flops_per_launch"] / avg_s / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp32_peak, "traffic": traffic,
+                    "peak_source": "FP32: 152 SMs x 128 lanes x 2 flops x max SM clock (" + peak_kind + " clock)",
+                    "hbm_achieved_gbs": hbm_achieved, "hbm_frac": hbm_achieved / hbm_peak}
+    else:
+        roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": hbm_achieved / hbm_peak, "traffic": traffic, "peak_source": peak_kind}
+    roofline["kernel"] = dom
+    roofline["algorithmic_bytes_per_launch"] = prof[dom]["bytes_per_launch"]
+    roofline["algorithmic_flops_per_launch"] = prof[dom]["flops_per_launch"]
+    roofline["avg_launch_us"] = avg_s * 1e6
+    roofline["per_kernel"] = {
+        k: {"avg_us": 1e3 * v["total_ms"] / max(1, v["launches"]), "launches": v["launches"],
+            "GBps": v["bytes_per_launch"] / (v["total_ms"] / 1e3 / v["launches"]) / 1e9 if v["launches"] else None,
+            "TFLOPs": v["flops_per_launch"] / (v["total_ms"] / 1e3 / v["launches"]) / 1e12 if v["launches"] else None,
+            "share_of_step": v["total_ms"] / 1e3 / dt if dt else None}
+        for k, v in prof.items()}
 
     # end to end through the public API with host buffers: H2D of the visibilities, uvw and sky,
     # prediction, cold start, 30 iterations, D2H of the solutions.
@@ -314,7 +331,7 @@ def run_ours(args, world, rank, local):
             "config": {"workload": WORKLOAD, "stations": prob["N"], "baselines": prob["B"], "directions": prob["K"],
                        "subbands": prob["P"], "intervals": prob["I"], "samples": 10, "admm_iters": n_admm,
                        "n_lm": N_LM, "n_cg": N_CG, "basis": "Bernstein degree 3", "rho": 10.0,
-                       "formulation": args.formulation, "fused_lm": bool(args.fused_lm),
+                       "formulation": args.formulation,
                        "step": "predict + cold start + 30 C-ADMM iterations",
                        "l2": "inputs larger than L2 (436 MB per residual sweep, 242 MB per Hessian sweep)",
                        "parallelism": f"replica x{world}" if world > 1 else "single GPU",
@@ -339,7 +356,6 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--chunk-diagonals", type=int, default=0)
     ap.add_argument("--formulation", choices=["statistics", "direct"], default="statistics")
-    ap.add_argument("--fused-lm", action="store_true", help="finish LM/PCG steps inside the sweeps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run one launch of each sweep on the workload and exit (profiler captures)")

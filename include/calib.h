@@ -73,8 +73,6 @@ typedef struct {
     int chunk_diagonals;               /* baseline diagonals per CTA in the sweeps; 0 = automatic */
     void* cuda_stream;                 /* cudaStream_t to run on; NULL = the library creates one */
     int formulation;                   /* CALIB_FORM_STATISTICS (default) or CALIB_FORM_DIRECT */
-    int fused_lm;                      /* statistics form only: 1 = finish each agent's PCG / LM step in the
-                                          last CTA of its sweep; 0 (default) = separate per-agent launches */
 } calib_options;
 
 /* One record per C-ADMM iteration (Section 4 definitions, summed/averaged over all intervals):
@@ -173,11 +171,12 @@ int calib_sync(calib_ctx* ctx);
 /* Per-kernel timing over the following calib_admm_iter calls (CUDA events recorded
  * on the library stream around every launch of the sweep kernels when enabled). Kinds:
  * sweep_residual (direct residual/trial), sweep_hessvec (direct Hessian), stats_hessvec and
- * stats_trial (sufficient-statistics passes); bytes_per_launch are the algorithmic bytes.
- * names/ms/launches receive up to cap entries; returns the number of kernel kinds. */
+ * stats_trial (sufficient-statistics passes); bytes_per_launch and flops_per_launch are the
+ * algorithmic bytes and real flops (complex multiply 6, complex multiply-add 8) of one launch.
+ * Every output array may be NULL and receives up to cap entries; returns the number of kinds. */
 int calib_profile_enable(calib_ctx* ctx, int on);
 int calib_profile_read(calib_ctx* ctx, int cap, const char** names, double* total_ms,
-                       long long* launches, double* bytes_per_launch);
+                       long long* launches, double* bytes_per_launch, double* flops_per_launch);
 
 /* Autotuner: time the sweeps of one LM step (n_cg Hessian passes and one trial pass) on the
  * loaded data for 1, 2, 4, ... diagonals per CTA and the whole agent per CTA, and keep the

@@ -32,7 +32,7 @@ EXPORTED = [
 class CalibOptions(C.Structure):
     _fields_ = [("n_intervals", C.c_int), ("n_samples", C.c_int), ("samples_per_agent", C.POINTER(C.c_int32)),
                 ("n_lm", C.c_int), ("n_cg", C.c_int), ("chunk_diagonals", C.c_int), ("cuda_stream", C.c_void_p),
-                ("formulation", C.c_int), ("fused_lm", C.c_int)]
+                ("formulation", C.c_int)]
 
 
 class CalibStats(C.Structure):
@@ -74,7 +74,7 @@ def load(path: str = LIB_PATH):
         "calib_hessvec": (i, [vp, vp, vp, vp, i]),
         "calib_sync": (i, [vp]),
         "calib_profile_enable": (i, [vp, i]),
-        "calib_profile_read": (i, [vp, i, vp, vp, vp, vp]),
+        "calib_profile_read": (i, [vp, i, vp, vp, vp, vp, vp]),
         "calib_launch_count": (C.c_longlong, [vp]),
         "calib_last_error": (C.c_char_p, []),
         "calib_destroy": (None, [vp]),
@@ -134,8 +134,7 @@ def calib_default_options() -> CalibOptions:
 
 
 def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, samples_per_agent=None,
-               n_lm=10, n_cg=4, chunk_diagonals=0, cuda_stream=None, formulation=CALIB_FORM_STATISTICS,
-               fused_lm=0):
+               n_lm=10, n_cg=4, chunk_diagonals=0, cuda_stream=None, formulation=CALIB_FORM_STATISTICS):
     lib = load()
     pq_a = np.ascontiguousarray(pq, dtype=np.int32)
     fr = np.ascontiguousarray(freqs_hz, dtype=np.float64)
@@ -145,7 +144,6 @@ def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, sa
     opt.n_intervals, opt.n_samples, opt.n_lm, opt.n_cg = n_intervals, n_samples, n_lm, n_cg
     opt.chunk_diagonals = chunk_diagonals
     opt.formulation = formulation
-    opt.fused_lm = int(fused_lm)
     spa = None
     if samples_per_agent is not None:
         spa = np.ascontiguousarray(samples_per_agent, dtype=np.int32)
@@ -246,8 +244,11 @@ def calib_profile_read(ctx):
     ms = np.zeros(cap)
     n = np.zeros(cap, dtype=np.int64)
     by = np.zeros(cap)
-    cnt = load().calib_profile_read(ctx, cap, C.cast(names, C.c_void_p), ms.ctypes.data, n.ctypes.data, by.ctypes.data)
-    return {names[i].decode(): dict(total_ms=float(ms[i]), launches=int(n[i]), bytes_per_launch=float(by[i]))
+    fl = np.zeros(cap)
+    cnt = load().calib_profile_read(ctx, cap, C.cast(names, C.c_void_p), ms.ctypes.data, n.ctypes.data,
+                                    by.ctypes.data, fl.ctypes.data)
+    return {names[i].decode(): dict(total_ms=float(ms[i]), launches=int(n[i]), bytes_per_launch=float(by[i]),
+                                    flops_per_launch=float(fl[i]))
             for i in range(cnt)}
 
 

@@ -1,8 +1,10 @@
 // Internal declarations shared by the CUDA translation units of libcalib.so.
 //
 // Device data layout (all float32 unless noted; "block" = one 2x2 complex matrix = 8 floats):
-//   J, Jt, Y, BZ, gradg, gradg_t, grad, x, r, z, p   [A][K][N][8]
+//   J, Jt, Y, BZ, gradg, grad, x, r, p   [A][K][N][8]
 //   Gm        [A][K][N][4]   Jacobi blocks G_pk (Hermitian): g00, g11, re g01, im g01
+//   gw        [A][K][N][N]   Jacobi weights: gw[a][k][o][p] = s_bk = sum_t |c_btk|^2 of the baseline
+//                            b = (p, o) (0 where flagged or o = p); G_pk = sum_o gw[a][k][o][p] J_ok^H J_ok
 //   part      [A][n_chunks][K][N][8]  per-CTA partial station sums of a baseline sweep
 //   part_cost [A][n_chunks]  float64 partial data cost
 //   Z, Zprev  [I][K][M][N][8] float64
@@ -80,16 +82,15 @@ struct SweepArgs {
 struct LMArgs {
     const float* part; const double* part_cost; const double* part_dcost; int n_chunks;
     float* J; float* Jt; const float* Y; const float* BZ;
-    float* gradg; float* grad; float* x; float* r; float* z; float* p; float* Ap;
+    float* gradg; float* grad; float* x; float* r; float* p;
     float* Gm;
+    const float* gw;        // [A][K][N][N] Jacobi weights
     AgentState* st;
     const float* rho;       // [K]
-    const DiagDesc* desc; const int* slot; const float* spow;   // for the Jacobi blocks
-    const int* inc_off;     // [A][N+1] start of each station's incidence list in inc
-    const int2* inc;        // (global slot, other station) per incident baseline, slot order
     int A, N, K, D;
     double tau;
     int cost_from_decrease;  // trial cost g(J') = g(J) - decrease (statistics sweeps carry no cost)
+    int timing;              // autotuner: PCG step runs its whole path and writes no agent state
 };
 
 struct ConsArgs {
@@ -116,8 +117,8 @@ int sweep_threads(int slots_max);
 // ---- launchers (lm.cu)
 enum LMEvalMode : int { LM_BEGIN_FROM_PARTIALS = 0, LM_BEGIN_REUSE = 1, LM_ACCEPT = 2 };
 cudaError_t launch_lm_eval(const LMArgs& a, int mode, cudaStream_t s);
-cudaError_t launch_cg_step(const LMArgs& a, cudaStream_t s);
-cudaError_t launch_lm_trial(const LMArgs& a, cudaStream_t s);
+// One PCG step; with last set it also forms the LM trial point Jt = J + x and the predicted decrease.
+cudaError_t launch_cg_step(const LMArgs& a, bool last, cudaStream_t s);
 cudaError_t launch_eval_output(const LMArgs& a, float* grad_out, double* L_out, double* g_out, cudaStream_t s);
 cudaError_t launch_hv_output(const LMArgs& a, float* out, cudaStream_t s);
 
@@ -150,8 +151,8 @@ struct PredictArgs {
     int A, P, N, K, S, D, Tmax;
 };
 cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s);
-cudaError_t launch_coh_power(const float2* C, const DiagDesc* desc, const int* T, float* spow,
-                             int A, int D, int K, cudaStream_t s);
+cudaError_t launch_gram_weights(const float2* C, const DiagDesc* desc, const int* slot, const int* T, float* gw,
+                                int A, int D, int K, int N, cudaStream_t s);
 cudaError_t launch_check_finite(const float* x, long long n, int* status, cudaStream_t s);
 cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc,
                             const int* T, int A, int D, int K, cudaStream_t s);
@@ -163,11 +164,6 @@ struct SSArgs {
     const float* J; const float* eta;   // eta: direction (Hessian) or LM step x (trial)
     float* part; double* part_dcost; int* status;
     int A, N, K, D, n_chunks, chunk_diags, slots_max;
-    // Finishing the agent's LM/PCG step in the last CTA to complete its chunks:
-    int fuse;        // 0: sweep only; 1: Hessian -> PCG step (+ LM trial point if last_cg), trial -> LM accept
-    int last_cg;     // this Hessian sweep feeds the last PCG step of the LM step
-    int* arrive;     // [A] chunk arrival counters (zero between launches)
-    LMArgs lm;
 };
 cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, cudaStream_t s);
 cudaError_t prepare_ss_kernels();

@@ -70,25 +70,23 @@ struct calib_ctx {
     // layout (depends on flags)
     std::vector<DiagDesc> desc_h;
     std::vector<int> slot_h, slot_b_h;
-    std::vector<int> inc_off_h;
-    std::vector<int2> inc_h;
     long long int_v = 0, int_c = 0;             // internal totals (float2)
     long long int_u = 0, int_s = 0;             // sufficient-statistics totals (float2)
     double alg_bytes[4] = {0, 0, 0, 0};         // algorithmic bytes per launch of each sweep kind
+    double alg_flops[4] = {0, 0, 0, 0};         // algorithmic real flops per launch of each sweep kind
     std::vector<uint8_t> flags_h;
 
     // device
     float2 *V = nullptr, *C = nullptr, *ssU = nullptr, *ssS = nullptr;
     int formulation = 0;  // 0 sufficient statistics, 1 direct
-    int fused_lm = 0;     // statistics form: LM/PCG steps inside the sweeps' last CTA per agent
     bool ss_dirty = true;
     DiagDesc* desc = nullptr;
-    int *slot = nullptr, *slot_b = nullptr, *T_d = nullptr, *inc_off = nullptr;
+    int *slot = nullptr, *slot_b = nullptr, *T_d = nullptr;
     int2* inc = nullptr;
-    float* spow = nullptr;
+    float* gw = nullptr;  // [A][K][N][N] Jacobi weights
     long long *vis_off_d = nullptr, *coh_off_d = nullptr;
     float *J = nullptr, *Jt = nullptr, *Y = nullptr, *BZ = nullptr, *gradg = nullptr, *grad = nullptr;
-    float *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *Gm = nullptr;
+    float *x = nullptr, *r = nullptr, *p = nullptr, *Gm = nullptr;
     float *evJ = nullptr, *evE = nullptr, *evOut = nullptr;
     float* part = nullptr;
     double* part_cost = nullptr;
@@ -102,7 +100,6 @@ struct calib_ctx {
     int max_iters = 0;
     int* iter_counter = nullptr;
     int* status = nullptr;
-    int* arrive = nullptr;
     double* evL = nullptr;
     double* evG = nullptr;
     void* staging = nullptr;
@@ -162,17 +159,11 @@ LMArgs lm_args(calib_ctx* c) {
     a.grad = c->grad;
     a.x = c->x;
     a.r = c->r;
-    a.z = c->z;
     a.p = c->p;
-    a.Ap = c->Ap;
     a.Gm = c->Gm;
     a.st = c->st;
     a.rho = c->rho_d;
-    a.desc = c->desc;
-    a.slot = c->slot;
-    a.spow = c->spow;
-    a.inc_off = c->inc_off;
-    a.inc = c->inc;
+    a.gw = c->gw;
     a.A = c->A;
     a.N = c->N;
     a.K = c->K;
@@ -184,8 +175,6 @@ LMArgs lm_args(calib_ctx* c) {
 
 SSArgs ss_args(calib_ctx* c, const float* J, const float* eta) {
     SSArgs a{};
-    a.lm = lm_args(c);
-    a.arrive = c->arrive;
     a.U = c->ssU;
     a.S = c->ssS;
     a.desc = c->desc;
@@ -272,11 +261,9 @@ void free_layout(calib_ctx* c) {
     cudaFree(c->desc); c->desc = nullptr;
     cudaFree(c->slot); c->slot = nullptr;
     cudaFree(c->slot_b); c->slot_b = nullptr;
-    cudaFree(c->spow); c->spow = nullptr;
+    cudaFree(c->gw); c->gw = nullptr;
     cudaFree(c->ssU); c->ssU = nullptr;
     cudaFree(c->ssS); c->ssS = nullptr;
-    cudaFree(c->inc_off); c->inc_off = nullptr;
-    cudaFree(c->inc); c->inc = nullptr;
 }
 
 void clear_graphs(calib_ctx* c) {
@@ -302,6 +289,7 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     const int KK = K * (K + 1) / 2;
     int smax = 4;
     double alg_res = 0, alg_hv = 0, alg_ssh = 0, alg_sst = 0;
+    double flo[4] = {0, 0, 0, 0};
     for (int a = 0; a < A; ++a) {
         for (int d = 1; d <= D; ++d) {
             DiagDesc& dd = c->desc_h[(size_t)a * D + d - 1];
@@ -334,27 +322,14 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
             alg_hv += (double)n * c->T[a] * (8.0 * K);
             alg_ssh += (double)n * 8.0 * KK;
             alg_sst += (double)n * (32.0 * K + 8.0 * KK);
-        }
-    }
-    // station-incidence lists per agent (global slot, other station), in slot order
-    c->inc_off_h.assign((size_t)A * (N + 1), 0);
-    c->inc_h.assign(2 * c->slot_h.size(), int2{0, 0});
-    {
-        size_t pos = 0;
-        for (int a = 0; a < A; ++a) {
-            const int s0 = c->desc_h[(size_t)a * D].slot_off;
-            const int s1 = (a + 1 < A) ? c->desc_h[(size_t)(a + 1) * D].slot_off : (int)c->slot_h.size();
-            std::vector<std::vector<int2>> lists(N);
-            for (int s = s0; s < s1; ++s) {
-                const int f = c->slot_h[s] & 0xff, sc = (c->slot_h[s] >> 8) & 0xff;
-                lists[f].push_back(int2{s, sc});
-                lists[sc].push_back(int2{s, f});
-            }
-            for (int p = 0; p < N; ++p) {
-                c->inc_off_h[(size_t)a * (N + 1) + p] = (int)pos;
-                for (const int2& e : lists[p]) c->inc_h[pos++] = e;
-            }
-            c->inc_off_h[(size_t)a * (N + 1) + N] = (int)pos;
+            // Real flops per baseline (complex multiply 6, complex multiply-add 8, 2x2 complex
+            // product 56): P_l / Q_l per direction, the per-sample or S-weighted direction sums,
+            // and the two station terms per direction with their accumulation (128).
+            const double T = c->T[a];
+            flo[0] += (double)n * (T * (64.0 * K + 8.0) + 56.0 * K + 128.0 * K);
+            flo[1] += (double)n * (T * 64.0 * K + 120.0 * K + 128.0 * K);
+            flo[2] += (double)n * (248.0 * K + 32.0 * K * K);
+            flo[3] += (double)n * (432.0 * K + 64.0 * K * K);
         }
     }
     c->int_v = voff;
@@ -366,6 +341,7 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     c->alg_bytes[1] = alg_hv;
     c->alg_bytes[2] = alg_ssh;
     c->alg_bytes[3] = alg_sst;
+    for (int i = 0; i < 4; ++i) c->alg_flops[i] = flo[i];
     c->TT_res = sweep_tile_samples(smax, K, false);
     c->TT_hv = sweep_tile_samples(smax, K, true);
     if (sweep_threads(smax) > 512) return fail(CALIB_EINVAL, "too many stations for one CTA per diagonal");
@@ -378,12 +354,7 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     CK(dalloc(&c->desc, c->desc_h.size()));
     CK(dalloc(&c->slot, c->slot_h.size()));
     CK(dalloc(&c->slot_b, c->slot_b_h.size()));
-    CK(dalloc(&c->spow, c->slot_h.size() * (size_t)K));
-    CK(dalloc(&c->inc_off, c->inc_off_h.size()));
-    CK(dalloc(&c->inc, c->inc_h.size()));
-    CK(cudaMemcpy(c->inc_off, c->inc_off_h.data(), c->inc_off_h.size() * sizeof(int), cudaMemcpyHostToDevice));
-    if (!c->inc_h.empty())
-        CK(cudaMemcpy(c->inc, c->inc_h.data(), c->inc_h.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CK(dalloc(&c->gw, (size_t)A * K * N * N));
     CK(dalloc(&c->ssU, (size_t)c->int_u));
     CK(dalloc(&c->ssS, (size_t)c->int_s));
     CK(cudaMemcpy(c->desc, c->desc_h.data(), c->desc_h.size() * sizeof(DiagDesc), cudaMemcpyHostToDevice));
@@ -449,7 +420,7 @@ struct Enq {
         if (err == cudaSuccess && e != cudaSuccess) err = e;
         ge->kernels += 1;
     }
-    void sweep(int mode, const float* J, const float* eta, int fuse = 0, int last_cg = 0) {
+    void sweep(int mode, const float* J, const float* eta) {
         ProfPair pp{};
         const bool prof = c->profiling;
         const bool ss = c->formulation == 0 && mode != SWEEP_RESIDUAL;
@@ -460,10 +431,7 @@ struct Enq {
             cudaEventRecordWithFlags(pp.a, c->stream, cudaEventRecordExternal);
         }
         if (ss) {
-            SSArgs sa = ss_args(c, J, eta);
-            sa.fuse = fuse;
-            sa.last_cg = last_cg;
-            ok(launch_ss_sweep(sa, mode == SWEEP_HESSVEC, c->stream));
+            ok(launch_ss_sweep(ss_args(c, J, eta), mode == SWEEP_HESSVEC, c->stream));
         } else {
             ok(launch_sweep(sweep_args(c, mode, J, eta), mode, c->stream));
         }
@@ -484,15 +452,13 @@ void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
     } else {
         q.ok(launch_lm_eval(la, LM_BEGIN_REUSE, c->stream));
     }
-    const bool fused = c->formulation == 0 && c->fused_lm;  // sweeps finish the LM/PCG steps themselves
     for (int l = 0; l < c->n_lm; ++l) {
         for (int k = 0; k < c->n_cg; ++k) {
-            q.sweep(SWEEP_HESSVEC, c->J, c->p, fused ? 1 : 0, k == c->n_cg - 1 ? 1 : 0);
-            if (!fused) q.ok(launch_cg_step(la, c->stream));
+            q.sweep(SWEEP_HESSVEC, c->J, c->p);
+            q.ok(launch_cg_step(la, k == c->n_cg - 1, c->stream));  // the last one forms the trial point
         }
-        if (!fused) q.ok(launch_lm_trial(la, c->stream));
-        q.sweep(SWEEP_TRIAL, c->J, c->x, fused ? 1 : 0);
-        if (!fused) q.ok(launch_lm_eval(la, LM_ACCEPT, c->stream));
+        q.sweep(SWEEP_TRIAL, c->J, c->x);
+        q.ok(launch_lm_eval(la, LM_ACCEPT, c->stream));
     }
     if (gauge) q.ok(launch_gauge(ca, c->stream));
     q.ok(launch_zupdate(ca, c->stream));
@@ -526,9 +492,10 @@ std::map<TuneKey, int>& tune_cache() {
     return m;
 }
 
-// Time the sweeps of one LM step (n_cg Hessian passes + one trial pass, without the fused LM
-// work) for candidate numbers of diagonals per CTA and keep the fastest. Runs on the context's
-// data; leaves the iteration state untouched (sweep outputs are scratch).
+// Time one LM step (n_cg Hessian passes and PCG steps, one trial pass and its reduction) for
+// candidate numbers of diagonals per CTA and keep the fastest. Runs on the context's data; touches
+// only scratch outputs and the PCG vectors x, r, p, which the next LM begin re-initialises (the
+// PCG steps run in timing mode and write no agent state).
 int autotune(calib_ctx* c) {
     long long work = 0;
     for (const DiagDesc& d : c->desc_h) work += (long long)d.n * (c->formulation == 0 ? 1 : 1);
@@ -561,6 +528,7 @@ int autotune(calib_ctx* c) {
         // the next LM begin re-initialises.
         LMArgs la = lm_args(c);
         la.Jt = c->J;
+        la.timing = 1;
         auto one_step = [&]() -> cudaError_t {
             cudaError_t err = cudaSuccess;
             for (int k = 0; k < c->n_cg && err == cudaSuccess; ++k) {
@@ -571,7 +539,7 @@ int autotune(calib_ctx* c) {
                     err = launch_sweep(sweep_args(c, SWEEP_HESSVEC, c->J, c->p), SWEEP_HESSVEC, c->stream);
                 }
                 la.n_chunks = c->n_chunks;
-                if (err == cudaSuccess) err = launch_cg_step(la, c->stream);
+                if (err == cudaSuccess) err = launch_cg_step(la, false, c->stream);
             }
             if (err != cudaSuccess) return err;
             if (c->formulation == 0) {
@@ -625,7 +593,6 @@ void calib_default_options(calib_options* opt) {
     opt->chunk_diagonals = 0;
     opt->cuda_stream = nullptr;
     opt->formulation = CALIB_FORM_STATISTICS;
-    opt->fused_lm = 0;
 }
 
 int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* pq, int n_dirs, int n_freqs,
@@ -675,7 +642,6 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     c->n_lm = opt.n_lm;
     c->n_cg = opt.n_cg;
     c->formulation = opt.formulation;
-    c->fused_lm = opt.fused_lm ? 1 : 0;
     c->pq.assign(pq, pq + 2 * (size_t)B);
     c->freqs.assign(freqs_hz, freqs_hz + P);
     c->basis.assign(basis, basis + (size_t)P * M);
@@ -721,7 +687,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
 
     const size_t vec = (size_t)A * K * N * 8;
     bool okm = true;
-    for (float** pp : {&c->J, &c->Jt, &c->Y, &c->BZ, &c->gradg, &c->grad, &c->x, &c->r, &c->z, &c->p, &c->Ap,
+    for (float** pp : {&c->J, &c->Jt, &c->Y, &c->BZ, &c->gradg, &c->grad, &c->x, &c->r, &c->p,
                        &c->evJ, &c->evE, &c->evOut})
         okm = okm && dalloc(pp, vec) == cudaSuccess;
     okm = okm && dalloc(&c->Gm, (size_t)A * K * N * 4) == cudaSuccess;
@@ -735,7 +701,6 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     okm = okm && dalloc(&c->freqs_d, (size_t)P) == cudaSuccess && dalloc(&c->rho_d, (size_t)K) == cudaSuccess;
     okm = okm && dalloc(&c->st, (size_t)A) == cudaSuccess && dalloc(&c->prim, (size_t)A * K) == cudaSuccess;
     okm = okm && dalloc(&c->dual2, (size_t)c->I * K) == cudaSuccess;
-    okm = okm && dalloc(&c->arrive, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->iter_counter, 1) == cudaSuccess && dalloc(&c->status, 1) == cudaSuccess;
     okm = okm && dalloc(&c->evL, (size_t)A) == cudaSuccess && dalloc(&c->evG, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess;
@@ -819,7 +784,7 @@ int calib_set_data(calib_ctx* c, const void* vis, const void* coh, const uint8_t
         ia.dst = c->C;
         ia.is_vis = 0;
         CK(launch_ingest(ia, c->stream));
-        CK(launch_coh_power(c->C, c->desc, c->T_d, c->spow, c->A, c->D, c->K, c->stream));
+        CK(launch_gram_weights(c->C, c->desc, c->slot, c->T_d, c->gw, c->A, c->D, c->K, c->N, c->stream));
         c->launches += 3;
         c->coh_set = true;
     }
@@ -867,7 +832,7 @@ int calib_predict(calib_ctx* c, const double* uvw_m, const double* sky, int n_sr
     pa.D = c->D;
     pa.Tmax = Tmax;
     CK(launch_predict(pa, c->stream));
-    CK(launch_coh_power(c->C, c->desc, c->T_d, c->spow, c->A, c->D, c->K, c->stream));
+    CK(launch_gram_weights(c->C, c->desc, c->slot, c->T_d, c->gw, c->A, c->D, c->K, c->N, c->stream));
     c->launches += 2;
     c->ss_dirty = true;
     c->coh_set = true;
@@ -946,7 +911,6 @@ int calib_admm_iter(calib_ctx* c, int n_iters, calib_stats* hist) {
     if (rc) return rc;
     CK(cudaMemsetAsync(c->iter_counter, 0, sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
-    CK(cudaMemsetAsync(c->arrive, 0, (size_t)c->A * sizeof(int), c->stream));
     if (c->formulation == 0 && c->ss_dirty) {
         CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->T_d, c->A, c->D, c->K, c->stream));
         c->launches += 1;
@@ -1092,7 +1056,7 @@ int calib_profile_enable(calib_ctx* c, int on) {
 }
 
 int calib_profile_read(calib_ctx* c, int cap, const char** names, double* total_ms, long long* launches,
-                       double* bytes_per_launch) {
+                       double* bytes_per_launch, double* flops_per_launch) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     static const char* kNames[4] = {"sweep_residual", "sweep_hessvec", "stats_hessvec", "stats_trial"};
     for (int i = 0; i < 4 && i < cap; ++i) {
@@ -1100,6 +1064,7 @@ int calib_profile_read(calib_ctx* c, int cap, const char** names, double* total_
         if (total_ms) total_ms[i] = c->prof_ms[i];
         if (launches) launches[i] = c->prof_n[i];
         if (bytes_per_launch) bytes_per_launch[i] = c->alg_bytes[i];
+        if (flops_per_launch) flops_per_launch[i] = c->alg_flops[i];
     }
     return 4;
 }
@@ -1211,11 +1176,11 @@ void calib_destroy(calib_ctx* c) {
     clear_graphs(c);
     free_layout(c);
     for (void* p : {(void*)c->J, (void*)c->Jt, (void*)c->Y, (void*)c->BZ, (void*)c->gradg, (void*)c->grad,
-                    (void*)c->x, (void*)c->r, (void*)c->z, (void*)c->p, (void*)c->Ap, (void*)c->Gm,
+                    (void*)c->x, (void*)c->r, (void*)c->p, (void*)c->Gm,
                     (void*)c->evJ, (void*)c->evE, (void*)c->evOut, (void*)c->part, (void*)c->part_cost, (void*)c->part_dcost,
                     (void*)c->Z, (void*)c->Zprev, (void*)c->basis_d, (void*)c->Pinv_d, (void*)c->freqs_d,
                     (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->dual2, (void*)c->stats, (void*)c->iter_counter,
-                    (void*)c->status, (void*)c->arrive, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
+                    (void*)c->status, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
                     (void*)c->coh_off_d, c->staging, (void*)c->ws_prev, (void*)c->ws_mlp, (void*)c->ws_L,
                     (void*)c->xf_d, (void*)c->ws_chose})
         if (p) cudaFree(p);

@@ -136,9 +136,15 @@ __global__ void __launch_bounds__(256) k_predict(const PredictArgs a, int s_chun
     }
 }
 
-// s_bk = sum_t |c_btk|^2 per slot and direction (fixed for the whole calibration).
-__global__ void k_coh_power(const float2* C, const DiagDesc* desc, const int* T, float* spow, int D, int K) {
+// Jacobi weights of one agent: gw[k][o][p] = gw[k][p][o] = s_bk = sum_t |c_btk|^2 for the baseline
+// b = (p, o), zero for flagged baselines and o = p (fixed for the whole calibration). Each entry is
+// written by the one slot that holds its station pair: no atomics.
+__global__ void k_gram_weights(const float2* C, const DiagDesc* desc, const int* slot, const int* T, float* gw,
+                               int D, int K, int N) {
     const int agent = blockIdx.x;
+    float* W = gw + (size_t)agent * K * N * N;
+    for (int i = threadIdx.x; i < K * N * N; i += blockDim.x) W[i] = 0.f;
+    __syncthreads();
     const int Ta = T[agent];
     for (int d = 0; d < D; ++d) {
         const DiagDesc dsc = desc[(size_t)agent * D + d];
@@ -149,7 +155,10 @@ __global__ void k_coh_power(const float2* C, const DiagDesc* desc, const int* T,
                 const float2 c = C[dsc.coff + ((size_t)t * dsc.n_pad + g) * K + k];
                 s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
             }
-            spow[((size_t)dsc.slot_off + g) * K + k] = s;
+            const int sl = slot[dsc.slot_off + g];
+            const int f = sl & 0xff, sc = (sl >> 8) & 0xff;
+            W[((size_t)k * N + f) * N + sc] = s;
+            W[((size_t)k * N + sc) * N + f] = s;
         }
     }
 }
@@ -228,9 +237,9 @@ cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s) {
     k_predict<<<grid, 256, smem, s>>>(a, s_chunk);
     return cudaGetLastError();
 }
-cudaError_t launch_coh_power(const float2* C, const DiagDesc* desc, const int* T, float* spow,
-                             int A, int D, int K, cudaStream_t s) {
-    k_coh_power<<<A, 256, 0, s>>>(C, desc, T, spow, D, K);
+cudaError_t launch_gram_weights(const float2* C, const DiagDesc* desc, const int* slot, const int* T, float* gw,
+                                int A, int D, int K, int N, cudaStream_t s) {
+    k_gram_weights<<<A, 256, 0, s>>>(C, desc, slot, T, gw, D, K, N);
     return cudaGetLastError();
 }
 cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc,

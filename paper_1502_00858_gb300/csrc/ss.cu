@@ -12,11 +12,7 @@
 // Mapping, per-station scatter and the bounded mbarrier/TMA-bulk ring follow sweep.cu: one CTA per
 // (agent, chunk of circulant diagonals), one stage per diagonal, four threads per slot (one per
 // correlation), two barrier-separated shared-memory phases per diagonal (no atomics).
-// With fuse set, the last CTA to finish an agent's chunks (fence + arrival counter) reduces the
-// partials in chunk order and completes the agent's PCG step (Hessian pass) or LM accept/reject
-// step (trial pass) itself, so the per-agent LM work needs no launch of its own.
 #include "calib_internal.cuh"
-#include "lm_device.cuh"
 
 namespace calib {
 namespace {
@@ -292,24 +288,6 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
             double s = 0.0;
             for (int w = 0; w < (nthr >> 5); ++w) s += red[w];
             a.part_dcost[(size_t)agent * a.n_chunks + chunk] = s;
-        }
-    }
-    if (a.fuse) {
-        __shared__ int last_s;
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) last_s = atomicAdd(&a.arrive[agent], 1) == a.n_chunks - 1;
-        __syncthreads();
-        if (last_s) {
-            __threadfence();
-            if (HV) {
-                cg_step_dev(a.lm, agent, red);
-                if (a.last_cg) lm_trial_dev(a.lm, agent, red);
-            } else {
-                // Js/Es are free now: 2*K*N*4 floats of scratch for the Jacobi blocks
-                lm_eval_dev(a.lm, agent, LM_ACCEPT, reinterpret_cast<float*>(Js), red);
-            }
-            if (tid == 0) a.arrive[agent] = 0;
         }
     }
 }

@@ -30,8 +30,7 @@ from synth import make_problem, user_layout
 pytestmark = pytest.mark.gpu
 
 REL_ADMM = 1e-4
-FORMS = {"statistics": capi.CALIB_FORM_STATISTICS, "direct": capi.CALIB_FORM_DIRECT,
-         "statistics_fused": capi.CALIB_FORM_STATISTICS}
+FORMS = {"statistics": capi.CALIB_FORM_STATISTICS, "direct": capi.CALIB_FORM_DIRECT}
 _ORACLE_CACHE = {}
 
 
@@ -148,7 +147,7 @@ def test_predict_matches_oracle(lib, case):
 
 
 def run_both(lib, prob, n_iter, n_lm=10, n_cg=4, form="statistics"):
-    cal = calibrator(lib, prob, n_lm=n_lm, n_cg=n_cg, formulation=FORMS[form], fused_lm=form.endswith("fused"))
+    cal = calibrator(lib, prob, n_lm=n_lm, n_cg=n_cg, formulation=FORMS[form])
     hist = cal.iterate(n_iter)
     ref = O.admm(rounded(prob), n_iter, n_lm=n_lm, n_cg=n_cg)["hist"]
     return cal, hist, ref
@@ -198,7 +197,7 @@ def test_full_size_lofar_interval_sample(lib, form):
     10 samples) in the benchmark's launch configuration; the oracle recomputes interval 0."""
     prob = make_problem("lofar_n62_k5")
     n_iter = 2
-    cal = calibrator(lib, prob, formulation=FORMS[form], fused_lm=form.endswith("fused"))
+    cal = calibrator(lib, prob, formulation=FORMS[form])
     hist = cal.iterate(n_iter)
     L, g = cal.agent_objective()
     if "lofar" not in _ORACLE_CACHE:  # the oracle's interval 0 serves both formulations
