@@ -197,7 +197,7 @@ def run_ours(args, world, rank, local):
     stream = torch.cuda.Stream()
     cal = Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
                      n_intervals=prob["I"], samples=prob["T"], n_lm=N_LM, n_cg=N_CG,
-                     chunk_diagonals=args.chunk_diagonals, cuda_stream=stream.cuda_stream,
+                     chunk_diagonals=args.chunk_diagonals, ctas_per_sm=args.ctas_per_sm, cuda_stream=stream.cuda_stream,
                      formulation=capi.CALIB_FORM_DIRECT if args.formulation == "direct" else capi.CALIB_FORM_STATISTICS)
     dev = torch.device("cuda", local)
     vis_d = torch.from_numpy(ul["vis"].view(np.float32)).to(dev)
@@ -224,6 +224,12 @@ def run_ours(args, world, rank, local):
         capi.calib_predict(cal.ctx, uvw_d, sky_d, prob["f0"])
         capi.calib_reset(cal.ctx)
         capi.calib_admm_iter(cal.ctx, n_admm, want_hist=False)
+
+    # the sweep split the autotuner picks for this shape (what the first calib_admm_iter would do)
+    capi.calib_predict(cal.ctx, uvw_d, sky_d, prob["f0"])
+    split, split_ms = (args.ctas_per_sm if args.formulation == "statistics" else args.chunk_diagonals), None
+    if split == 0:
+        split, split_ms = capi.calib_autotune(cal.ctx)
 
     def barrier():
         if world > 1:
@@ -332,6 +338,8 @@ def run_ours(args, world, rank, local):
                        "subbands": prob["P"], "intervals": prob["I"], "samples": 10, "admm_iters": n_admm,
                        "n_lm": N_LM, "n_cg": N_CG, "basis": "Bernstein degree 3", "rho": 10.0,
                        "formulation": args.formulation,
+                       ("ctas_per_sm" if args.formulation == "statistics" else "chunk_diagonals"): split,
+                       "autotune_ms_per_lm_step": split_ms,
                        "step": "predict + cold start + 30 C-ADMM iterations",
                        "l2": "inputs larger than L2 (436 MB per residual sweep, 242 MB per Hessian sweep)",
                        "parallelism": f"replica x{world}" if world > 1 else "single GPU",
@@ -354,7 +362,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--chunk-diagonals", type=int, default=0)
+    ap.add_argument("--chunk-diagonals", type=int, default=0, help="direct sweeps: diagonals per CTA (0 = tuned)")
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="statistics sweeps: CTAs per SM (0 = tuned)")
     ap.add_argument("--formulation", choices=["statistics", "direct"], default="statistics")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true",

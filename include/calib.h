@@ -70,9 +70,12 @@ typedef struct {
     const int32_t* samples_per_agent;  /* [A] samples of each agent, or NULL (host pointer, copied) */
     int n_lm;                          /* LM steps per J-update (default 10) */
     int n_cg;                          /* PCG steps per LM step (default 4) */
-    int chunk_diagonals;               /* baseline diagonals per CTA in the sweeps; 0 = automatic */
+    int chunk_diagonals;               /* direct sweeps: baseline diagonals per CTA; 0 = automatic */
     void* cuda_stream;                 /* cudaStream_t to run on; NULL = the library creates one */
     int formulation;                   /* CALIB_FORM_STATISTICS (default) or CALIB_FORM_DIRECT */
+    int ctas_per_sm;                   /* statistics sweeps: grid = SMs * ctas_per_sm CTAs (at most one
+                                          per agent-diagonal), each taking an equal contiguous share of
+                                          the (agent, diagonal) items; 0 = automatic */
 } calib_options;
 
 /* One record per C-ADMM iteration (Section 4 definitions, summed/averaged over all intervals):
@@ -178,14 +181,15 @@ int calib_profile_enable(calib_ctx* ctx, int on);
 int calib_profile_read(calib_ctx* ctx, int cap, const char** names, double* total_ms,
                        long long* launches, double* bytes_per_launch, double* flops_per_launch);
 
-/* Autotuner: time the sweeps of one LM step (n_cg Hessian passes and one trial pass) on the
- * loaded data for 1, 2, 4, ... diagonals per CTA and the whole agent per CTA, and keep the
- * fastest (the CTA-to-work split of every sweep launch). calib_admm_iter runs it by itself
- * before its first iteration when calib_options.chunk_diagonals is 0; the choice is cached per
- * problem shape for the process. This call re-measures. Outputs (host, any may be NULL): the
- * chosen value, up to cap candidates and their milliseconds per LM step, and the candidate count.
- * The iteration state (J, Z, Y) is not changed. */
-int calib_autotune(calib_ctx* ctx, int* chunk_diagonals, int cap, int* candidates,
+/* Autotuner: time one LM step (n_cg Hessian passes with their PCG steps, one trial pass and its
+ * reduction) on the loaded data for each candidate work split and keep the fastest. The split is
+ * CTAs per SM (1, 2, 3, 4, 6, 8, 12, 16, 24) for CALIB_FORM_STATISTICS and diagonals per CTA
+ * (1, 2, 4, ..., N/2) for CALIB_FORM_DIRECT. calib_admm_iter runs it by itself before its first
+ * iteration when the option that fixes the split (ctas_per_sm or chunk_diagonals) is 0; the
+ * choice is cached per problem shape for the process. This call re-measures. Outputs (host, any
+ * may be NULL): the chosen split, up to cap candidates and their milliseconds per LM step, and the
+ * candidate count. The iteration state (J, Z, Y) is not changed. */
+int calib_autotune(calib_ctx* ctx, int* split, int cap, int* candidates,
                    double* ms_per_lm_step, int* n_candidates);
 
 /* ---- Learned warm start (the paper starts a calibration from the previous time slot's solution,

@@ -32,7 +32,7 @@ EXPORTED = [
 class CalibOptions(C.Structure):
     _fields_ = [("n_intervals", C.c_int), ("n_samples", C.c_int), ("samples_per_agent", C.POINTER(C.c_int32)),
                 ("n_lm", C.c_int), ("n_cg", C.c_int), ("chunk_diagonals", C.c_int), ("cuda_stream", C.c_void_p),
-                ("formulation", C.c_int)]
+                ("formulation", C.c_int), ("ctas_per_sm", C.c_int)]
 
 
 class CalibStats(C.Structure):
@@ -134,7 +134,8 @@ def calib_default_options() -> CalibOptions:
 
 
 def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, samples_per_agent=None,
-               n_lm=10, n_cg=4, chunk_diagonals=0, cuda_stream=None, formulation=CALIB_FORM_STATISTICS):
+               n_lm=10, n_cg=4, chunk_diagonals=0, cuda_stream=None, formulation=CALIB_FORM_STATISTICS,
+               ctas_per_sm=0):
     lib = load()
     pq_a = np.ascontiguousarray(pq, dtype=np.int32)
     fr = np.ascontiguousarray(freqs_hz, dtype=np.float64)
@@ -144,6 +145,7 @@ def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, sa
     opt.n_intervals, opt.n_samples, opt.n_lm, opt.n_cg = n_intervals, n_samples, n_lm, n_cg
     opt.chunk_diagonals = chunk_diagonals
     opt.formulation = formulation
+    opt.ctas_per_sm = ctas_per_sm
     spa = None
     if samples_per_agent is not None:
         spa = np.ascontiguousarray(samples_per_agent, dtype=np.int32)
@@ -272,7 +274,8 @@ def calib_eval_noalloc(n_agents, n_stations, n_baselines, n_dirs, n_samples, pq,
 
 
 def calib_autotune(ctx):
-    """Re-measure the sweep split; returns (chosen diagonals per CTA, {candidate: ms per LM step})."""
+    """Re-measure the sweep split; returns (chosen split, {candidate: ms per LM step}). The split is
+    CTAs per SM (statistics form) or diagonals per CTA (direct form)."""
     cap = 64
     chosen = C.c_int()
     cand = np.zeros(cap, dtype=np.int32)

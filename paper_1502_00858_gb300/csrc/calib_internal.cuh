@@ -5,8 +5,9 @@
 //   Gm        [A][K][N][4]   Jacobi blocks G_pk (Hermitian): g00, g11, re g01, im g01
 //   gw        [A][K][N][N]   Jacobi weights: gw[a][k][o][p] = s_bk = sum_t |c_btk|^2 of the baseline
 //                            b = (p, o) (0 where flagged or o = p); G_pk = sum_o gw[a][k][o][p] J_ok^H J_ok
-//   part      [A][n_chunks][K][N][8]  per-CTA partial station sums of a baseline sweep
-//   part_cost [A][n_chunks]  float64 partial data cost
+//   part      [A][stride][K][N][8]  partial station sums of a baseline sweep (per chunk for the direct
+//                                   sweeps, per (agent, CTA) piece for the statistics sweeps)
+//   part_cost [A][stride]  float64 partial data cost
 //   Z, Zprev  [I][K][M][N][8] float64
 //
 // Sufficient statistics of a slot (C = c I_2 and J constant over the interval make them exact):
@@ -80,7 +81,10 @@ struct SweepArgs {
 };
 
 struct LMArgs {
-    const float* part; const double* part_cost; const double* part_dcost; int n_chunks;
+    // Partials of the preceding sweep: agent a's pieces j < part_n[a] (part_stride for every agent
+    // when part_n is NULL) at part[(a * part_stride + j) * K*N*8], part_cost / part_dcost[a * part_stride + j].
+    const float* part; const double* part_cost; const double* part_dcost;
+    const int* part_n; int part_stride;
     float* J; float* Jt; const float* Y; const float* BZ;
     float* gradg; float* grad; float* x; float* r; float* p;
     float* Gm;
@@ -163,9 +167,13 @@ struct SSArgs {
     const DiagDesc* desc; const int* slot;
     const float* J; const float* eta;   // eta: direction (Hessian) or LM step x (trial)
     float* part; double* part_dcost; int* status;
-    int A, N, K, D, n_chunks, chunk_diags, slots_max;
+    int A, N, K, D, slots_max;
+    int part_stride;   // pieces per agent in part / part_dcost (>= the CTAs meeting any one agent)
 };
-cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, cudaStream_t s);
+// grid CTAs split the A*D (agent, diagonal) items into equal contiguous ranges; 1 <= grid <= A*D.
+cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, int grid, cudaStream_t s);
+size_t ss_sweep_smem_bytes(int N, int K, int slots_max, bool hessvec, int* stage_bytes);
+int ss_sweep_threads(int slots_max);
 cudaError_t prepare_ss_kernels();
 
 // One-time kernel attribute set-up (dynamic shared memory limits); call before any capture.

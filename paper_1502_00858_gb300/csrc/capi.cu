@@ -54,7 +54,10 @@ struct calib_ctx {
     int dev = 0;
     int N = 0, B = 0, K = 0, P = 0, M = 0, I = 0, A = 0, D = 0;
     int n_lm = 10, n_cg = 4, chunk_diags = 1, n_chunks = 1, slots_max = 4;
-    bool tune_pending = false;     // chunk size chosen by the autotuner at the first iteration
+    bool tune_pending = false;     // work split chosen by the autotuner at the first iteration
+    // statistics sweeps: grid = sms * ctas_per_sm CTAs (at most A*D), balanced contiguous item ranges
+    int sms = 1, ctas_per_sm = 4, grid_ss = 1, stride_ss = 1;
+    int* pn_ss = nullptr;          // [A] pieces (CTAs) meeting each agent
     std::vector<std::pair<int, double>> tune_log;  // (diagonals per CTA, ms per LM step)
     int TT_res = 1, TT_hv = 1;
     cudaStream_t stream = nullptr;
@@ -145,12 +148,15 @@ SweepArgs sweep_args(calib_ctx* c, int mode, const float* J, const float* eta) {
     return a;
 }
 
-LMArgs lm_args(calib_ctx* c) {
+// ss_parts: the partials come from a statistics sweep (per-agent piece counts), else from a
+// direct sweep (n_chunks per agent).
+LMArgs lm_args(calib_ctx* c, bool ss_parts) {
     LMArgs a{};
     a.part = c->part;
     a.part_cost = c->part_cost;
     a.part_dcost = c->part_dcost;
-    a.n_chunks = c->n_chunks;
+    a.part_n = ss_parts ? c->pn_ss : nullptr;
+    a.part_stride = ss_parts ? c->stride_ss : c->n_chunks;
     a.J = c->J;
     a.Jt = c->Jt;
     a.Y = c->Y;
@@ -188,10 +194,30 @@ SSArgs ss_args(calib_ctx* c, const float* J, const float* eta) {
     a.N = c->N;
     a.K = c->K;
     a.D = c->D;
-    a.n_chunks = c->n_chunks;
-    a.chunk_diags = c->chunk_diags;
     a.slots_max = c->slots_max;
+    a.part_stride = c->stride_ss;
     return a;
+}
+
+// Split the A*D items of the statistics sweeps over grid = min(A*D, sms * m) CTAs and record how
+// many CTAs meet each agent (the pieces its reductions sum). CTA c takes items
+// [floor(c W / G), floor((c+1) W / G)); item i lies in CTA ((i+1) G - 1) / W.
+int set_partition(calib_ctx* c, int m) {
+    const long long W = (long long)c->A * c->D;
+    const long long G = std::max(1LL, std::min(W, (long long)c->sms * m));
+    std::vector<int> pn(c->A);
+    int stride = 1;
+    for (int a = 0; a < c->A; ++a) {
+        const long long c0 = (((long long)a * c->D + 1) * G - 1) / W;
+        const long long c1 = (((long long)a * c->D + c->D) * G - 1) / W;
+        pn[a] = (int)(c1 - c0 + 1);
+        stride = std::max(stride, pn[a]);
+    }
+    CK(cudaMemcpy(c->pn_ss, pn.data(), pn.size() * sizeof(int), cudaMemcpyHostToDevice));
+    c->ctas_per_sm = m;
+    c->grid_ss = (int)G;
+    c->stride_ss = stride;
+    return CALIB_OK;
 }
 
 ConsArgs cons_args(calib_ctx* c) {
@@ -347,6 +373,8 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     if (sweep_threads(smax) > 512) return fail(CALIB_EINVAL, "too many stations for one CTA per diagonal");
     if ((size_t)3 * 24 * 1024 + sweep_smem_bytes(N, K, true) + 4096 > 200 * 1024)
         return fail(CALIB_EINVAL, "N*K too large for the sweep kernels' shared memory");
+    if (c->formulation == 0 && ss_sweep_smem_bytes(N, K, smax, false, nullptr) > 200 * 1024)
+        return fail(CALIB_EINVAL, "N*K too large for the statistics sweeps' shared memory; use CALIB_FORM_DIRECT");
 
     free_layout(c);
     CK(dalloc(&c->V, (size_t)c->int_v));
@@ -431,7 +459,7 @@ struct Enq {
             cudaEventRecordWithFlags(pp.a, c->stream, cudaEventRecordExternal);
         }
         if (ss) {
-            ok(launch_ss_sweep(ss_args(c, J, eta), mode == SWEEP_HESSVEC, c->stream));
+            ok(launch_ss_sweep(ss_args(c, J, eta), mode == SWEEP_HESSVEC, c->grid_ss, c->stream));
         } else {
             ok(launch_sweep(sweep_args(c, mode, J, eta), mode, c->stream));
         }
@@ -444,11 +472,11 @@ struct Enq {
 
 void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
     calib_ctx* c = q.c;
-    const LMArgs la = lm_args(c);
+    const LMArgs la = lm_args(c, c->formulation == 0);  // after the iteration's own sweeps
     const ConsArgs ca = cons_args(c);
-    if (eval_first) {
+    if (eval_first) {  // the residual sweep is the direct one in both formulations (it yields g exactly)
         q.sweep(SWEEP_RESIDUAL, c->J, nullptr);
-        q.ok(launch_lm_eval(la, LM_BEGIN_FROM_PARTIALS, c->stream));
+        q.ok(launch_lm_eval(lm_args(c, false), LM_BEGIN_FROM_PARTIALS, c->stream));
     } else {
         q.ok(launch_lm_eval(la, LM_BEGIN_REUSE, c->stream));
     }
@@ -492,62 +520,72 @@ std::map<TuneKey, int>& tune_cache() {
     return m;
 }
 
-// Time one LM step (n_cg Hessian passes and PCG steps, one trial pass and its reduction) for
-// candidate numbers of diagonals per CTA and keep the fastest. Runs on the context's data; touches
-// only scratch outputs and the PCG vectors x, r, p, which the next LM begin re-initialises (the
-// PCG steps run in timing mode and write no agent state).
+// Time one LM step (n_cg Hessian passes and PCG steps, one trial pass and its reduction) for each
+// candidate work split and keep the fastest: CTAs per SM of the statistics sweeps, or diagonals per
+// CTA of the direct sweeps. Runs on the context's data; touches only scratch outputs and the PCG
+// vectors x, r, p, which the next LM begin re-initialises (the PCG steps run in timing mode and
+// write no agent state).
+int apply_split(calib_ctx* c, int v) {
+    if (c->formulation == 0) return set_partition(c, v);
+    c->chunk_diags = v;
+    c->n_chunks = (c->D + v - 1) / v;
+    return CALIB_OK;
+}
+
 int autotune(calib_ctx* c) {
     long long work = 0;
-    for (const DiagDesc& d : c->desc_h) work += (long long)d.n * (c->formulation == 0 ? 1 : 1);
+    for (const DiagDesc& d : c->desc_h) work += (long long)d.n;
     for (int a = 0; a < c->A && c->formulation == 1; ++a) work += (long long)c->T[a];
     const TuneKey key{c->N, c->K, c->A, c->D, c->formulation, c->n_cg, work};
     auto hit = tune_cache().find(key);
     c->tune_log.clear();
     if (hit != tune_cache().end()) {
-        c->chunk_diags = hit->second;
-        c->n_chunks = (c->D + c->chunk_diags - 1) / c->chunk_diags;
+        const int rc = apply_split(c, hit->second);
+        if (rc) return rc;
         c->tune_pending = false;
         clear_graphs(c);
         return CALIB_OK;
     }
     std::vector<int> cands;
-    for (int cd = 1; cd <= c->D; cd *= 2) cands.push_back(cd);
-    if (cands.back() != c->D) cands.push_back(c->D);
+    if (c->formulation == 0) {
+        const long long W = (long long)c->A * c->D;
+        long long last_grid = -1;
+        for (int m : {1, 2, 3, 4, 6, 8, 12, 16, 24}) {
+            const long long grid = std::min(W, (long long)c->sms * m);
+            if (grid == last_grid) break;  // capped at one item per CTA
+            cands.push_back(m);
+            last_grid = grid;
+        }
+    } else {
+        for (int cd = 1; cd <= c->D; cd *= 2) cands.push_back(cd);
+        if (cands.back() != c->D) cands.push_back(c->D);
+    }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     double best = 1e300;
-    int best_cd = c->chunk_diags;
+    int best_v = cands.front();
     const int reps = 3;
-    for (int cd : cands) {
-        c->chunk_diags = cd;
-        c->n_chunks = (c->D + cd - 1) / cd;
-        // One LM step's sweeps plus the per-agent reductions of their chunk partials (which grow
-        // with the chunk count): the stand-alone PCG step after each Hessian sweep and the gradient
-        // reduction after the trial sweep. These touch only PCG vectors and scratch outputs, which
-        // the next LM begin re-initialises.
-        LMArgs la = lm_args(c);
+    for (int v : cands) {
+        const int rc = apply_split(c, v);
+        if (rc) return rc;
+        LMArgs la = lm_args(c, c->formulation == 0);
         la.Jt = c->J;
         la.timing = 1;
         auto one_step = [&]() -> cudaError_t {
             cudaError_t err = cudaSuccess;
             for (int k = 0; k < c->n_cg && err == cudaSuccess; ++k) {
-                if (c->formulation == 0) {
-                    SSArgs sa = ss_args(c, c->J, c->p);
-                    err = launch_ss_sweep(sa, true, c->stream);
-                } else {
+                if (c->formulation == 0)
+                    err = launch_ss_sweep(ss_args(c, c->J, c->p), true, c->grid_ss, c->stream);
+                else
                     err = launch_sweep(sweep_args(c, SWEEP_HESSVEC, c->J, c->p), SWEEP_HESSVEC, c->stream);
-                }
-                la.n_chunks = c->n_chunks;
                 if (err == cudaSuccess) err = launch_cg_step(la, false, c->stream);
             }
             if (err != cudaSuccess) return err;
-            if (c->formulation == 0) {
-                SSArgs sa = ss_args(c, c->J, c->x);
-                err = launch_ss_sweep(sa, false, c->stream);
-            } else {
+            if (c->formulation == 0)
+                err = launch_ss_sweep(ss_args(c, c->J, c->x), false, c->grid_ss, c->stream);
+            else
                 err = launch_sweep(sweep_args(c, SWEEP_TRIAL, c->J, c->x), SWEEP_TRIAL, c->stream);
-            }
             if (err != cudaSuccess) return err;
             return launch_eval_output(la, c->evOut, c->evL, c->evG, c->stream);
         };
@@ -560,18 +598,18 @@ int autotune(calib_ctx* c) {
         CK(cudaEventElapsedTime(&ms, e0, e1));
         const double per = ms / reps;
         c->launches += (long long)(reps + 1) * (2 * c->n_cg + 2);
-        c->tune_log.emplace_back(cd, per);
+        c->tune_log.emplace_back(v, per);
         if (per < best) {
             best = per;
-            best_cd = cd;
+            best_v = v;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    c->chunk_diags = best_cd;
-    c->n_chunks = (c->D + best_cd - 1) / best_cd;
+    const int rc = apply_split(c, best_v);
+    if (rc) return rc;
     c->tune_pending = false;
-    tune_cache()[key] = best_cd;
+    tune_cache()[key] = best_v;
     clear_graphs(c);
     return check_status(c);
 }
@@ -593,6 +631,7 @@ void calib_default_options(calib_options* opt) {
     opt->chunk_diagonals = 0;
     opt->cuda_stream = nullptr;
     opt->formulation = CALIB_FORM_STATISTICS;
+    opt->ctas_per_sm = 0;
 }
 
 int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* pq, int n_dirs, int n_freqs,
@@ -661,14 +700,20 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     }
     c->user_v = vo;
     c->user_c = co;
+    // Work split of the sweeps: fixed by the options, else provisional until the autotuner runs.
     if (opt.chunk_diagonals > 0) {
         c->chunk_diags = std::min(opt.chunk_diagonals, c->D);
     } else {
-        c->tune_pending = true;  // provisional choice below until calib_autotune runs
+        if (c->formulation == 1) c->tune_pending = true;
         const int want = std::max(1, std::min(c->D, (1216 + A - 1) / A));
         c->chunk_diags = (c->D + want - 1) / want;
     }
     c->n_chunks = (c->D + c->chunk_diags - 1) / c->chunk_diags;
+    if (opt.ctas_per_sm > 0) {
+        c->ctas_per_sm = opt.ctas_per_sm;
+    } else if (c->formulation == 0) {
+        c->tune_pending = true;
+    }
 
     auto bail = [&](int rc) { calib_destroy(c); return rc; };
     if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(fail(CALIB_ECUDA, "no CUDA device"));
@@ -703,7 +748,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     okm = okm && dalloc(&c->dual2, (size_t)c->I * K) == cudaSuccess;
     okm = okm && dalloc(&c->iter_counter, 1) == cudaSuccess && dalloc(&c->status, 1) == cudaSuccess;
     okm = okm && dalloc(&c->evL, (size_t)A) == cudaSuccess && dalloc(&c->evG, (size_t)A) == cudaSuccess;
-    okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess;
+    okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess && dalloc(&c->pn_ss, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->vis_off_d, (size_t)A) == cudaSuccess && dalloc(&c->coh_off_d, (size_t)A) == cudaSuccess;
     if (!okm) return bail(fail(CALIB_ENOMEM, "device allocation failed"));
     if (ensure_stats(c, 64) != CALIB_OK) return bail(CALIB_ENOMEM);
@@ -717,7 +762,11 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     cudaMemset(c->status, 0, sizeof(int));
     cudaMemset(c->st, 0, (size_t)A * sizeof(AgentState));
     cudaMemset(c->prim, 0, (size_t)A * K * sizeof(double));
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess || c->sms < 1)
+        return bail(fail(CALIB_ECUDA, "cannot read the SM count"));
     int rc = build_layout(c, nullptr);
+    if (rc) return bail(rc);
+    rc = set_partition(c, c->ctas_per_sm);
     if (rc) return bail(rc);
     rc = calib_reset(c);
     if (rc) return bail(rc);
@@ -1001,7 +1050,7 @@ int calib_eval(calib_ctx* c, const void* Jin, double* L, double* g, void* grad, 
     CK(cudaMemcpyAsync(c->evJ, Jin, vb, ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     CK(launch_sweep(sweep_args(c, SWEEP_RESIDUAL, c->evJ, nullptr), SWEEP_RESIDUAL, c->stream));
-    LMArgs la = lm_args(c);
+    LMArgs la = lm_args(c, false);  // after a direct sweep
     la.Jt = c->evJ;
     CK(launch_eval_output(la, c->evOut, c->evL, c->evG, c->stream));
     c->launches += 2;
@@ -1026,7 +1075,7 @@ int calib_hessvec(calib_ctx* c, const void* Jin, const void* eta, void* out, int
     CK(cudaMemcpyAsync(c->evE, eta, vb, kind, c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     CK(launch_sweep(sweep_args(c, SWEEP_HESSVEC, c->evJ, c->evE), SWEEP_HESSVEC, c->stream));
-    LMArgs la = lm_args(c);
+    LMArgs la = lm_args(c, false);  // after a direct sweep
     la.p = c->evE;
     CK(launch_hv_output(la, c->evOut, c->stream));
     c->launches += 2;
@@ -1121,7 +1170,7 @@ int calib_warm_start(calib_ctx* c, calib_mlp* mlp, const void* J_prev, const voi
                        ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     if (mlp) {
         CK(mlp_warm_rows(mlp, c->ws_prev, c->BZ, c->xf_d, c->K, c->N, c->A, c->ws_mlp, c->stream));
-        LMArgs la = lm_args(c);
+        LMArgs la = lm_args(c, false);  // after a direct sweep
         const float* starts[2] = {c->ws_mlp, c->ws_prev};
         for (int i = 0; i < 2; ++i) {
             CK(launch_sweep(sweep_args(c, SWEEP_RESIDUAL, starts[i], nullptr), SWEEP_RESIDUAL, c->stream));
@@ -1146,7 +1195,7 @@ int calib_warm_start(calib_ctx* c, calib_mlp* mlp, const void* J_prev, const voi
     return CALIB_OK;
 }
 
-int calib_autotune(calib_ctx* c, int* chunk_diagonals, int cap, int* cand, double* ms_per_lm_step, int* n_cand) {
+int calib_autotune(calib_ctx* c, int* split, int cap, int* cand, double* ms_per_lm_step, int* n_cand) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "set visibilities and coherencies first");
     if (c->formulation == 0 && c->ss_dirty) {
@@ -1158,7 +1207,7 @@ int calib_autotune(calib_ctx* c, int* chunk_diagonals, int cap, int* cand, doubl
     tune_cache().clear();
     const int rc = autotune(c);
     if (rc) return rc;
-    if (chunk_diagonals) *chunk_diagonals = c->chunk_diags;
+    if (split) *split = c->formulation == 0 ? c->ctas_per_sm : c->chunk_diags;
     const int n = (int)c->tune_log.size();
     for (int i = 0; i < n && i < cap; ++i) {
         if (cand) cand[i] = c->tune_log[i].first;
@@ -1180,7 +1229,7 @@ void calib_destroy(calib_ctx* c) {
                     (void*)c->evJ, (void*)c->evE, (void*)c->evOut, (void*)c->part, (void*)c->part_cost, (void*)c->part_dcost,
                     (void*)c->Z, (void*)c->Zprev, (void*)c->basis_d, (void*)c->Pinv_d, (void*)c->freqs_d,
                     (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->dual2, (void*)c->stats, (void*)c->iter_counter,
-                    (void*)c->status, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
+                    (void*)c->status, (void*)c->pn_ss, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
                     (void*)c->coh_off_d, c->staging, (void*)c->ws_prev, (void*)c->ws_mlp, (void*)c->ws_L,
                     (void*)c->xf_d, (void*)c->ws_chose})
         if (p) cudaFree(p);

@@ -109,11 +109,14 @@ __device__ __forceinline__ Blk precond(const Blk& x, const float (&G)[4], float 
     return z;
 }
 
-// Sum of the per-chunk partial station sums of a sweep, fixed chunk order.
+__device__ __forceinline__ int n_parts(const LMArgs& a, int agent) { return a.part_n ? a.part_n[agent] : a.part_stride; }
+
+// Sum of the partial station sums of a sweep, fixed piece order.
 __device__ __forceinline__ Blk sum_parts(const LMArgs& a, int agent, int blk, int KN) {
-    const float* base = a.part + (size_t)agent * a.n_chunks * KN * 8;
+    const float* base = a.part + (size_t)agent * a.part_stride * KN * 8;
     Blk s = ld_blk(base, blk);
-    for (int ch = 1; ch < a.n_chunks; ++ch) {
+    const int np = n_parts(a, agent);
+    for (int ch = 1; ch < np; ++ch) {
         const Blk q = ld_blk(base + (size_t)ch * KN * 8, blk);
 #pragma unroll
         for (int i = 0; i < 8; ++i) s.v[i] += q.v[i];
@@ -375,9 +378,10 @@ __global__ void __launch_bounds__(LM_MAX_THREADS) k_lm_eval(const LMArgs a, cons
         block_sum<2>(v, red[0]);
         if (tid == 0) {
             double g_t = 0.0, dg = 0.0;
-            for (int ch = 0; ch < a.n_chunks; ++ch) {
-                if (!a.cost_from_decrease) g_t += a.part_cost[(size_t)agent * a.n_chunks + ch];
-                dg += a.part_dcost[(size_t)agent * a.n_chunks + ch];
+            const int np = n_parts(a, agent);
+            for (int ch = 0; ch < np; ++ch) {
+                if (!a.cost_from_decrease) g_t += a.part_cost[(size_t)agent * a.part_stride + ch];
+                dg += a.part_dcost[(size_t)agent * a.part_stride + ch];
             }
             if (a.cost_from_decrease) g_t = st.g - dg;
             const double L_t = g_t + (double)v[0];
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(LM_MAX_THREADS) k_lm_eval(const LMArgs a, cons
         if (tid == 0) {
             if (mode == LM_BEGIN_FROM_PARTIALS) {
                 double g = 0.0;
-                for (int ch = 0; ch < a.n_chunks; ++ch) g += a.part_cost[(size_t)agent * a.n_chunks + ch];
+                for (int ch = 0; ch < n_parts(a, agent); ++ch) g += a.part_cost[(size_t)agent * a.part_stride + ch];
                 st.g = g;
             }
             st.L = st.g + (double)v[0];
@@ -622,7 +626,7 @@ __global__ void __launch_bounds__(256) k_eval_output(const LMArgs a, float* grad
     pen = block_sum_d(pen, red);
     if (threadIdx.x == 0) {
         double g = 0.0;
-        for (int ch = 0; ch < a.n_chunks; ++ch) g += a.part_cost[(size_t)agent * a.n_chunks + ch];
+        for (int ch = 0; ch < n_parts(a, agent); ++ch) g += a.part_cost[(size_t)agent * a.part_stride + ch];
         if (g_out) g_out[agent] = g;
         if (L_out) L_out[agent] = g + pen;
     }

@@ -9,9 +9,19 @@
 //                  dP_l = x_pl J_ql^H + J_pl x_ql^H + x_pl x_ql^H; the data-cost decrease is
 //                  g(J) - g(J') = sum_k Re <dP_k, 2 W_k - (S dP)_k> (Frobenius inner product).
 // The identities are exact; the per-pass work and traffic no longer depend on the number of samples.
-// Mapping, per-station scatter and the bounded mbarrier/TMA-bulk ring follow sweep.cu: one CTA per
-// (agent, chunk of circulant diagonals), one stage per diagonal, four threads per slot (one per
-// correlation), two barrier-separated shared-memory phases per diagonal (no atomics).
+//
+// Work split: the A*D (agent, circulant diagonal) items are cut into gridDim.x equal contiguous
+// ranges, one per CTA, and the grid is a multiple of the SM count, so every SM gets the same work
+// and there is no partial last wave. A CTA stages J and eta (or x) of its current agent in shared
+// memory, streams the per-slot statistics of one diagonal per stage through a cp.async.bulk ring
+// (mbarrier, bounded waits), and writes its station sums as one partial per (agent, piece) when the
+// agent changes; piece = the CTA's index among the CTAs whose range meets that agent.
+// Two threads per slot, one per row of the 2x2 blocks: thread rr forms row rr of Q_l (or P_l and
+// dP_l), of the S-weighted sums X_k and of the first station's term X_k J_s. The second station's
+// term X_k^H J_f needs column rr of X_k, whose other entry comes from the partner lane. Within a
+// diagonal every station is the first element of at most one slot and the second of at most one,
+// and first- and second-station sums are kept in separate arrays, so the shared-memory updates of a
+// diagonal are conflict-free and need no barrier between the two (no atomics).
 #include "calib_internal.cuh"
 
 namespace calib {
@@ -66,53 +76,39 @@ __device__ __forceinline__ void cmac(float2& acc, float2 s, float2 q) {
     acc.x = fmaf(s.x, q.x, fmaf(-s.y, q.y, acc.x));
     acc.y = fmaf(s.x, q.y, fmaf(s.y, q.x, acc.y));
 }
-__device__ __forceinline__ float2 shfl2(float2 v, int src) {
-    return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+// value of the partner lane (lane ^ 1: the other row of the same slot)
+__device__ __forceinline__ float2 shfl2x(float2 v) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1));
 }
 
 // KB: register bucket; EXACT: K == KB, so every loop bound and packed-S index is a constant.
+// CTA holding item i of W items split into G equal contiguous ranges (start(c) = floor(c W / G)).
+__device__ __forceinline__ long long cta_of_item(long long i, long long W, long long G) { return ((i + 1) * G - 1) / W; }
+
+// KB: register bucket; EXACT: K == KB, so every loop bound and packed-S index is a constant.
 template <int KB, bool HV, bool EXACT>
-__global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stage_bytes) {
+__global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int stage_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int agent = blockIdx.y, chunk = blockIdx.x;
     const int N = a.N, D = a.D;
     const int K = EXACT ? KB : a.K;
     const int KK = K * (K + 1) / 2;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int g = tid >> 2, e = tid & 3;
-    const int lane = tid & 31, gbase = lane & ~3;
-    const int rr = e >> 1, cc = e & 1;
-    const int KN4 = K * N * 4;
+    const int g = tid >> 1, rr = tid & 1;
+    const int lane = tid & 31;
+    const int KN2 = K * N * 2;  // float4 per vector: [K][N][row]
 
     unsigned char* stage = smem;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NST * stage_bytes);
-    float2* Js = reinterpret_cast<float2*>(smem + NST * stage_bytes + BAR_BYTES);  // [K][N][4]
-    float2* Es = Js + KN4;                                // [K][N][4] eta or x
-    float2* acc = Es + KN4;                               // [K][N][4] first-station sums
-    // Hessian pass: second-station sums in their own array, so the two scatter phases of a
-    // diagonal need no barrier between them (the next diagonal's stage barrier orders them).
-    float2* accs = HV ? acc + KN4 : acc;
-    double* red = reinterpret_cast<double*>(accs + KN4);  // [64]
+    float4* Js = reinterpret_cast<float4*>(smem + NST * stage_bytes + BAR_BYTES);  // [K][N][2 rows]
+    float4* Es = Js + KN2;     // eta (Hessian) or x (trial)
+    float4* acc = Es + KN2;    // first-station sums
+    float4* accs = acc + KN2;  // second-station sums
+    double* red = reinterpret_cast<double*>(accs + KN2);  // [32]
 
-    {   // stage J and eta / x, clear the sums: 16-byte accesses (a station block is 32 bytes)
-        const float4* Jg = reinterpret_cast<const float4*>(a.J) + (size_t)agent * KN4 / 2;
-        const float4* Eg = reinterpret_cast<const float4*>(a.eta) + (size_t)agent * KN4 / 2;
-        float4* J4 = reinterpret_cast<float4*>(Js);
-        float4* E4 = reinterpret_cast<float4*>(Es);
-        float4* A4 = reinterpret_cast<float4*>(acc);
-        float4* S4 = reinterpret_cast<float4*>(accs);
-        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int i = tid; i < KN4 / 2; i += nthr) {
-            J4[i] = __ldg(Jg + i);
-            E4[i] = __ldg(Eg + i);
-            A4[i] = z4;
-            if (HV) S4[i] = z4;
-        }
-    }
-    const int d0 = 1 + chunk * a.chunk_diags;
-    const int d1 = min(D, d0 + a.chunk_diags - 1);
-    const int S = d1 >= d0 ? d1 - d0 + 1 : 0;  // one stage per diagonal
-    const DiagDesc* dsc_agent = a.desc + (size_t)agent * D;
+    const long long W = (long long)a.A * D, G = gridDim.x;
+    const long long i0 = (long long)blockIdx.x * W / G;
+    const int S = (int)((long long)(blockIdx.x + 1) * W / G - i0);
 
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) mbar_init(&bar[i], 1);
@@ -120,8 +116,13 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
     }
     __syncthreads();
 
+    auto desc_of = [&](int s2) -> DiagDesc {
+        const long long it = i0 + s2;
+        const long long ag = it / D;
+        return a.desc[(size_t)ag * D + (size_t)(it - ag * D)];
+    };
     auto issue = [&](int s2) {
-        const DiagDesc d2 = dsc_agent[d0 + s2 - 1];
+        const DiagDesc d2 = desc_of(s2);
         const uint32_t ub = HV ? 0u : (uint32_t)(d2.n_pad * K * 32);
         const uint32_t sb = (uint32_t)(d2.n_pad * KK * 8);
         unsigned char* buf = stage + (s2 % NST) * stage_bytes;
@@ -133,10 +134,52 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
     if (tid == 0)
         for (int s2 = 0; s2 < min(NST - 1, S); ++s2) issue(s2);
 
+    // Station sums of the finished agent -> its partial; call from uniform control flow after a barrier.
+    auto flush = [&](int ag, double dc) {
+        const long long piece = blockIdx.x - cta_of_item((long long)ag * D, W, G);
+        const size_t slot_p = (size_t)ag * a.part_stride + (size_t)piece;
+        float4* out = reinterpret_cast<float4*>(a.part) + slot_p * KN2;
+        for (int i = tid; i < KN2; i += nthr) {
+            const float4 u = acc[i], w = accs[i];
+            out[i] = make_float4(u.x + w.x, u.y + w.y, u.z + w.z, u.w + w.w);
+        }
+        if (!HV) {
+            for (int o = 16; o > 0; o >>= 1) dc += __shfl_down_sync(0xffffffffu, dc, o);
+            if (lane == 0) red[tid >> 5] = dc;
+            __syncthreads();
+            if (tid == 0) {
+                double t = 0.0;
+                for (int w = 0; w < (nthr >> 5); ++w) t += red[w];
+                a.part_dcost[slot_p] = t;
+            }
+        }
+    };
+
+    int agent = -1;
     double dcost = 0.0;
     for (int s = 0; s < S; ++s) {
-        const DiagDesc dsc = dsc_agent[d0 + s - 1];
-        __syncthreads();  // the buffer of stage s + NST - 1 is free
+        const long long it = i0 + s;
+        const int ag = (int)(it / D);
+        if (ag != agent) {
+            if (agent >= 0) {
+                __syncthreads();  // every thread is done with the previous agent's stage and sums
+                flush(agent, dcost);
+                dcost = 0.0;
+                __syncthreads();  // the sums are read out before they are cleared
+            }
+            agent = ag;
+            const float4* Jg = reinterpret_cast<const float4*>(a.J) + (size_t)ag * KN2;
+            const float4* Eg = reinterpret_cast<const float4*>(a.eta) + (size_t)ag * KN2;
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = tid; i < KN2; i += nthr) {
+                Js[i] = __ldg(Jg + i);
+                Es[i] = __ldg(Eg + i);
+                acc[i] = z4;
+                accs[i] = z4;
+            }
+        }
+        const DiagDesc dsc = desc_of(s);
+        __syncthreads();  // the buffer of stage s + NST - 1 is free; the agent's J / eta are staged
         if (tid == 0 && s + NST - 1 < S) {
             fence_proxy_async_smem();
             issue(s + NST - 1);
@@ -151,144 +194,127 @@ __global__ void __launch_bounds__(512) k_ss_sweep(const SSArgs a, const int stag
             return;
         }
         const unsigned char* buf = stage + (s % NST) * stage_bytes;
-        const float2* Us = reinterpret_cast<const float2*>(buf);  // [n_pad][K][4] (trial)
+        const float4* Us = reinterpret_cast<const float4*>(buf);  // [n_pad][K][2 rows] (trial)
         const float2* Ss = reinterpret_cast<const float2*>(buf + (HV ? 0 : dsc.n_pad * K * 32)) + (size_t)g * KK;
         const bool active = g < dsc.n;
         int first = 0, second = 0;
-        float2 X[KB];  // station terms are -X_k J_s (first) and -X_k^H J_f (second)
+        // Row rr of X_k: Hessian -(S Q)_k; trial W'_k = U_k - (S P)_k - (S dP)_k. Columns 0 and 1.
+        float2 X0[KB], X1[KB];
 #pragma unroll
-        for (int k = 0; k < KB; ++k) X[k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < KB; ++k) X0[k] = X1[k] = make_float2(0.f, 0.f);
         if (active) {
             const int sl = a.slot[dsc.slot_off + g];
             first = sl & 0xff;
             second = (sl >> 8) & 0xff;
-            float2 Pa[KB], Pb[KB];  // Hessian: Q; trial: P and dP
+            float2 Y0[HV ? 1 : KB], Y1[HV ? 1 : KB];    // trial: row rr of (S dP)_k
+            float2 dP0[HV ? 1 : KB], dP1[HV ? 1 : KB];  // trial: row rr of dP_l
+            if (!HV) {
+#pragma unroll
+                for (int k = 0; k < KB; ++k) Y0[k] = Y1[k] = dP0[k] = dP1[k] = make_float2(0.f, 0.f);
+            }
 #pragma unroll
             for (int l = 0; l < KB; ++l) {
-                if (l < K) {
-                    // row rr of J_f / eta_f and row cc of J_s / eta_s, one 16-byte load each
-                    const float4 jf = *reinterpret_cast<const float4*>(Js + (l * N + first) * 4 + rr * 2);
-                    const float4 js = *reinterpret_cast<const float4*>(Js + (l * N + second) * 4 + cc * 2);
-                    const float4 ef = *reinterpret_cast<const float4*>(Es + (l * N + first) * 4 + rr * 2);
-                    const float4 es = *reinterpret_cast<const float4*>(Es + (l * N + second) * 4 + cc * 2);
-                    const float2 jf0 = make_float2(jf.x, jf.y), jf1 = make_float2(jf.z, jf.w);
-                    const float2 js0 = make_float2(js.x, js.y), js1 = make_float2(js.z, js.w);
-                    const float2 ef0 = make_float2(ef.x, ef.y), ef1 = make_float2(ef.z, ef.w);
-                    const float2 es0 = make_float2(es.x, es.y), es1 = make_float2(es.z, es.w);
-                    const float2 jfs = f2add(cmul_cb(jf0, js0), cmul_cb(jf1, js1));
-                    const float2 efs = f2add(cmul_cb(ef0, js0), cmul_cb(ef1, js1));
-                    const float2 jfe = f2add(cmul_cb(jf0, es0), cmul_cb(jf1, es1));
-                    if (HV) {
-                        Pa[l] = f2add(efs, jfe);
-                    } else {
-                        const float2 efe = f2add(cmul_cb(ef0, es0), cmul_cb(ef1, es1));
-                        Pa[l] = jfs;
-                        Pb[l] = f2add(f2add(efs, jfe), efe);
-                    }
+                if (l >= K) continue;
+                // row rr of the first station's blocks, both rows of the second station's
+                const float4 jf = Js[(l * N + first) * 2 + rr], ef = Es[(l * N + first) * 2 + rr];
+                const float4 js0 = Js[(l * N + second) * 2 + 0], js1 = Js[(l * N + second) * 2 + 1];
+                const float4 es0 = Es[(l * N + second) * 2 + 0], es1 = Es[(l * N + second) * 2 + 1];
+                const float2 jf0 = make_float2(jf.x, jf.y), jf1 = make_float2(jf.z, jf.w);
+                const float2 ef0 = make_float2(ef.x, ef.y), ef1 = make_float2(ef.z, ef.w);
+                // (A B^H)[rr][c] = A[rr][0] conj(B[c][0]) + A[rr][1] conj(B[c][1]); B[c] = row c
+                const float2 js00 = make_float2(js0.x, js0.y), js01 = make_float2(js0.z, js0.w);
+                const float2 js10 = make_float2(js1.x, js1.y), js11 = make_float2(js1.z, js1.w);
+                const float2 es00 = make_float2(es0.x, es0.y), es01 = make_float2(es0.z, es0.w);
+                const float2 es10 = make_float2(es1.x, es1.y), es11 = make_float2(es1.z, es1.w);
+                float2 q0, q1, p0 = make_float2(0.f, 0.f), p1 = make_float2(0.f, 0.f);
+                const float2 efs0 = f2add(cmul_cb(ef0, js00), cmul_cb(ef1, js01));
+                const float2 efs1 = f2add(cmul_cb(ef0, js10), cmul_cb(ef1, js11));
+                const float2 jfe0 = f2add(cmul_cb(jf0, es00), cmul_cb(jf1, es01));
+                const float2 jfe1 = f2add(cmul_cb(jf0, es10), cmul_cb(jf1, es11));
+                if (HV) {
+                    q0 = f2add(efs0, jfe0);  // Q_l = eta_f J_s^H + J_f eta_s^H
+                    q1 = f2add(efs1, jfe1);
                 } else {
-                    Pa[l] = make_float2(0.f, 0.f);
-                    Pb[l] = make_float2(0.f, 0.f);
+                    q0 = f2add(cmul_cb(jf0, js00), cmul_cb(jf1, js01));  // P_l = J_f J_s^H
+                    q1 = f2add(cmul_cb(jf0, js10), cmul_cb(jf1, js11));
+                    // dP_l = x_f J_s^H + J_f x_s^H + x_f x_s^H
+                    p0 = f2add(f2add(efs0, jfe0), f2add(cmul_cb(ef0, es00), cmul_cb(ef1, es01)));
+                    p1 = f2add(f2add(efs1, jfe1), f2add(cmul_cb(ef0, es10), cmul_cb(ef1, es11)));
+                    dP0[l] = p0;
+                    dP1[l] = p1;
                 }
-            }
-            float dcf = 0.f;
-            // small exact K: the packed S of the slot in registers, each entry loaded once
-            constexpr bool SREG = EXACT && KB <= 6;
-            constexpr int KKR = SREG ? KB * (KB + 1) / 2 : 1;
-            float2 Sr[KKR];
-            if (SREG) {
 #pragma unroll
-                for (int i = 0; i < KKR; ++i) Sr[i] = Ss[i];
-            }
-#pragma unroll
-            for (int k = 0; k < KB; ++k) {
-                if (k < K) {
-                    float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
-#pragma unroll
-                    for (int l = 0; l < KB; ++l) {
-                        if (l < K) {
-                            // S_kl from the packed upper triangle; S_kl = conj(S_lk) below the diagonal
-                            const int lo = k < l ? k : l, hi = k < l ? l : k;
-                            const int si = lo * K - lo * (lo - 1) / 2 + (hi - lo);
-                            float2 skl = SREG ? Sr[si < KKR ? si : 0] : Ss[si];
-                            if (k > l) skl.y = -skl.y;
-                            cmac(sa, skl, Pa[l]);
-                            if (!HV) cmac(sb, skl, Pb[l]);
-                        }
-                    }
-                    if (HV) {
-                        X[k] = make_float2(-sa.x, -sa.y);  // X = -(S Q)_k
-                    } else {
-                        const float2 W = f2sub(Us[((size_t)g * K + k) * 4 + e], sa);  // W_k at J
-                        // decrease: Re[conj(dP_k) (2 W_k - (S dP)_k)]
-                        const float2 t = make_float2(2.f * W.x - sb.x, 2.f * W.y - sb.y);
-                        dcf = fmaf(Pb[k].x, t.x, fmaf(Pb[k].y, t.y, dcf));
-                        X[k] = f2sub(W, sb);  // W'_k at J' = J + x
+                for (int k = 0; k < KB; ++k) {
+                    if (k >= K) continue;
+                    // S_kl from the packed upper triangle; S_kl = conj(S_lk) below the diagonal
+                    const int lo = k < l ? k : l, hi = k < l ? l : k;
+                    float2 skl = Ss[lo * K - lo * (lo - 1) / 2 + (hi - lo)];
+                    if (k > l) skl.y = -skl.y;
+                    cmac(X0[k], skl, q0);
+                    cmac(X1[k], skl, q1);
+                    if (!HV) {
+                        cmac(Y0[k], skl, p0);
+                        cmac(Y1[k], skl, p1);
                     }
                 }
             }
-            dcost += (double)dcf;
+            if (HV) {
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    X0[k] = make_float2(-X0[k].x, -X0[k].y);
+                    X1[k] = make_float2(-X1[k].x, -X1[k].y);
+                }
+            } else {
+                float dcf = 0.f;
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    if (k >= K) continue;
+                    const float4 u = Us[((size_t)g * K + k) * 2 + rr];
+                    const float2 W0 = make_float2(u.x - X0[k].x, u.y - X0[k].y);  // W_k at J
+                    const float2 W1 = make_float2(u.z - X1[k].x, u.w - X1[k].y);
+                    // decrease: Re[conj(dP_k) (2 W_k - (S dP)_k)], this row
+                    dcf = fmaf(dP0[k].x, 2.f * W0.x - Y0[k].x, fmaf(dP0[k].y, 2.f * W0.y - Y0[k].y, dcf));
+                    dcf = fmaf(dP1[k].x, 2.f * W1.x - Y1[k].x, fmaf(dP1[k].y, 2.f * W1.y - Y1[k].y, dcf));
+                    X0[k] = f2sub(W0, Y0[k]);  // W'_k at J' = J + x
+                    X1[k] = f2sub(W1, Y1[k]);
+                }
+                dcost += (double)dcf;
+            }
         }
-        // Phase 1: first station receives -X_k J'_s (J' = J + x in the trial pass).
+        // First station: -= row rr of X_k J'_s (J' = J + x in the trial pass).
+        // Second station: -= row rr of X_k^H J'_f = conj(X[0][rr]) J'_f[0][.] + conj(X[1][rr]) J'_f[1][.].
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
-            if (k < K) {
-                const float2 w0 = shfl2(X[k], gbase + rr * 2 + 0);
-                const float2 w1 = shfl2(X[k], gbase + rr * 2 + 1);
-                if (active) {
-                    const float2* js = Js + (k * N + second) * 4;
-                    float2 j0 = js[0 * 2 + cc], j1 = js[1 * 2 + cc];
-                    if (!HV) {
-                        const float2* xs = Es + (k * N + second) * 4;
-                        j0 = f2add(j0, xs[0 * 2 + cc]);
-                        j1 = f2add(j1, xs[1 * 2 + cc]);
-                    }
-                    const float2 v = f2add(cmul(w0, j0), cmul(w1, j1));
-                    float2* dd = acc + (k * N + first) * 4 + e;
-                    *dd = f2sub(*dd, v);
-                }
+            if (k >= K) continue;
+            const float2 send = rr == 0 ? X1[k] : X0[k];  // X[rr][1-rr], wanted by the partner
+            const float2 oth = shfl2x(send);              // X[1-rr][rr]
+            if (!active) continue;
+            const float2 own = rr == 0 ? X0[k] : X1[k];   // X[rr][rr]
+            const float2 xc0 = rr == 0 ? own : oth, xc1 = rr == 0 ? oth : own;  // X[0][rr], X[1][rr]
+            float4 s0 = Js[(k * N + second) * 2 + 0], s1 = Js[(k * N + second) * 2 + 1];
+            float4 f0 = Js[(k * N + first) * 2 + 0], f1 = Js[(k * N + first) * 2 + 1];
+            if (!HV) {
+                s0 = f4add(s0, Es[(k * N + second) * 2 + 0]);
+                s1 = f4add(s1, Es[(k * N + second) * 2 + 1]);
+                f0 = f4add(f0, Es[(k * N + first) * 2 + 0]);
+                f1 = f4add(f1, Es[(k * N + first) * 2 + 1]);
             }
-        }
-        if (!HV) __syncthreads();
-        // Phase 2: second station receives -X_k^H J'_f.
-#pragma unroll
-        for (int k = 0; k < KB; ++k) {
-            if (k < K) {
-                const float2 w0 = shfl2(X[k], gbase + 0 * 2 + rr);
-                const float2 w1 = shfl2(X[k], gbase + 1 * 2 + rr);
-                if (active) {
-                    const float2* jf = Js + (k * N + first) * 4;
-                    float2 j0 = jf[0 * 2 + cc], j1 = jf[1 * 2 + cc];
-                    if (!HV) {
-                        const float2* xf = Es + (k * N + first) * 4;
-                        j0 = f2add(j0, xf[0 * 2 + cc]);
-                        j1 = f2add(j1, xf[1 * 2 + cc]);
-                    }
-                    const float2 v = f2add(cmul_ca(w0, j0), cmul_ca(w1, j1));
-                    float2* dd = accs + (k * N + second) * 4 + e;
-                    *dd = f2sub(*dd, v);
-                }
-            }
+            // (X J'_s)[rr][c] = X[rr][0] J'_s[0][c] + X[rr][1] J'_s[1][c]
+            const float2 v0 = f2add(cmul(X0[k], make_float2(s0.x, s0.y)), cmul(X1[k], make_float2(s1.x, s1.y)));
+            const float2 v1 = f2add(cmul(X0[k], make_float2(s0.z, s0.w)), cmul(X1[k], make_float2(s1.z, s1.w)));
+            float4* d1 = acc + (k * N + first) * 2 + rr;
+            float4 t1 = *d1;
+            *d1 = make_float4(t1.x - v0.x, t1.y - v0.y, t1.z - v1.x, t1.w - v1.y);
+            const float2 w0 = f2add(cmul_ca(xc0, make_float2(f0.x, f0.y)), cmul_ca(xc1, make_float2(f1.x, f1.y)));
+            const float2 w1 = f2add(cmul_ca(xc0, make_float2(f0.z, f0.w)), cmul_ca(xc1, make_float2(f1.z, f1.w)));
+            float4* d2 = accs + (k * N + second) * 2 + rr;
+            float4 t2 = *d2;
+            *d2 = make_float4(t2.x - w0.x, t2.y - w0.y, t2.z - w1.x, t2.w - w1.y);
         }
     }
-    __syncthreads();
-    float4* out = reinterpret_cast<float4*>(a.part) + ((size_t)agent * a.n_chunks + chunk) * KN4 / 2;
-    for (int i = tid; i < KN4 / 2; i += nthr) {
-        float4 v = reinterpret_cast<const float4*>(acc)[i];
-        if (HV) {
-            const float4 w = reinterpret_cast<const float4*>(accs)[i];
-            v = make_float4(v.x + w.x, v.y + w.y, v.z + w.z, v.w + w.w);
-        }
-        out[i] = v;
-    }
-    if (!HV) {
-        for (int o = 16; o > 0; o >>= 1) dcost += __shfl_down_sync(0xffffffffu, dcost, o);
-        if (lane == 0) red[tid >> 5] = dcost;
+    if (agent >= 0) {
         __syncthreads();
-        if (tid == 0) {
-            double s = 0.0;
-            for (int w = 0; w < (nthr >> 5); ++w) s += red[w];
-            a.part_dcost[(size_t)agent * a.n_chunks + chunk] = s;
-        }
+        flush(agent, dcost);
     }
 }
 
@@ -315,27 +341,27 @@ cudaError_t prep_all() {
 }
 
 template <int KB, bool HV>
-cudaError_t go(const SSArgs& a, int threads, size_t smem, int sb, cudaStream_t s) {
+cudaError_t go(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
     if (a.K == KB)
-        k_ss_sweep<KB, HV, true><<<dim3(a.n_chunks, a.A), threads, smem, s>>>(a, sb);
+        k_ss_sweep<KB, HV, true><<<grid, threads, smem, s>>>(a, sb);
     else
-        k_ss_sweep<KB, HV, false><<<dim3(a.n_chunks, a.A), threads, smem, s>>>(a, sb);
+        k_ss_sweep<KB, HV, false><<<grid, threads, smem, s>>>(a, sb);
     return cudaGetLastError();
 }
 
 template <bool HV>
-cudaError_t dispatch(const SSArgs& a, int threads, size_t smem, int sb, cudaStream_t s) {
+cudaError_t dispatch(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
     const int K = a.K;
-    if (K <= 1) return go<1, HV>(a, threads, smem, sb, s);
-    if (K <= 2) return go<2, HV>(a, threads, smem, sb, s);
-    if (K <= 3) return go<3, HV>(a, threads, smem, sb, s);
-    if (K <= 4) return go<4, HV>(a, threads, smem, sb, s);
-    if (K <= 5) return go<5, HV>(a, threads, smem, sb, s);
-    if (K <= 6) return go<6, HV>(a, threads, smem, sb, s);
-    if (K <= 8) return go<8, HV>(a, threads, smem, sb, s);
-    if (K <= 10) return go<10, HV>(a, threads, smem, sb, s);
-    if (K <= 12) return go<12, HV>(a, threads, smem, sb, s);
-    return go<16, HV>(a, threads, smem, sb, s);
+    if (K <= 1) return go<1, HV>(a, grid, threads, smem, sb, s);
+    if (K <= 2) return go<2, HV>(a, grid, threads, smem, sb, s);
+    if (K <= 3) return go<3, HV>(a, grid, threads, smem, sb, s);
+    if (K <= 4) return go<4, HV>(a, grid, threads, smem, sb, s);
+    if (K <= 5) return go<5, HV>(a, grid, threads, smem, sb, s);
+    if (K <= 6) return go<6, HV>(a, grid, threads, smem, sb, s);
+    if (K <= 8) return go<8, HV>(a, grid, threads, smem, sb, s);
+    if (K <= 10) return go<10, HV>(a, grid, threads, smem, sb, s);
+    if (K <= 12) return go<12, HV>(a, grid, threads, smem, sb, s);
+    return go<16, HV>(a, grid, threads, smem, sb, s);
 }
 
 }  // namespace
@@ -345,14 +371,22 @@ cudaError_t prepare_ss_kernels() {
     return e != cudaSuccess ? e : prep_all<true>();
 }
 
-cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, cudaStream_t s) {
-    const int KK = a.K * (a.K + 1) / 2;
-    const int per_slot = (hessvec ? 0 : a.K * 32) + KK * 8;
-    const int sb = ((a.slots_max * per_slot + 127) / 128) * 128;
-    const size_t smem = (size_t)NST * sb + BAR_BYTES + (size_t)(hessvec ? 4 : 3) * a.K * a.N * 32 + 64 * 8;
-    if (smem > 200 * 1024) return cudaErrorInvalidConfiguration;
-    const int threads = ((4 * a.slots_max + 31) / 32) * 32;
-    return hessvec ? dispatch<true>(a, threads, smem, sb, s) : dispatch<false>(a, threads, smem, sb, s);
+size_t ss_sweep_smem_bytes(int N, int K, int slots_max, bool hessvec, int* stage_bytes) {
+    const int KK = K * (K + 1) / 2;
+    const int per_slot = (hessvec ? 0 : K * 32) + KK * 8;
+    const int sb = ((slots_max * per_slot + 127) / 128) * 128;
+    if (stage_bytes) *stage_bytes = sb;
+    return (size_t)NST * sb + BAR_BYTES + (size_t)4 * K * N * 32 + 32 * 8;
+}
+
+int ss_sweep_threads(int slots_max) { return ((2 * slots_max + 31) / 32) * 32; }
+
+cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, int grid, cudaStream_t s) {
+    int sb = 0;
+    const size_t smem = ss_sweep_smem_bytes(a.N, a.K, a.slots_max, hessvec, &sb);
+    if (smem > 200 * 1024 || grid < 1 || (long long)grid > (long long)a.A * a.D) return cudaErrorInvalidConfiguration;
+    const int threads = ss_sweep_threads(a.slots_max);
+    return hessvec ? dispatch<true>(a, grid, threads, smem, sb, s) : dispatch<false>(a, grid, threads, smem, sb, s);
 }
 
 }  // namespace calib

@@ -222,8 +222,8 @@ def test_autotuner_picks_a_measured_split_and_results_do_not_depend_on_it(lib):
     chosen, table = capi.calib_autotune(cal.ctx)
     assert chosen in table and table[chosen] == min(table.values())
     h_tuned = cal.iterate(3)
-    for cd in (1, prob["N"] // 2):
-        other = calibrator(lib, prob, chunk_diagonals=cd)
+    for m in (1, 5):  # CTAs per SM of the statistics sweeps
+        other = calibrator(lib, prob, ctas_per_sm=m)
         h = other.iterate(3)
         for key in ("objective", "resid_norm"):
             np.testing.assert_allclose(h[key], h_tuned[key], rtol=1e-5)
