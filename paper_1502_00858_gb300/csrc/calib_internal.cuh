@@ -49,7 +49,7 @@ struct DiagDesc {     // one per (agent, diagonal)
     int slot_off;     // global index of the first slot of this diagonal in the slot arrays
     int n;            // active (unflagged) slots
     int n_pad;        // padded slot count (multiple of 4, >= n)
-    int pad_;
+    int pslot_off;    // index of this diagonal's n_pad slot words in the padded slot array (multiple of 4)
 };
 
 struct AgentState {   // per-agent scalars
@@ -164,7 +164,8 @@ cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2*
 // ---- launchers (ss.cu): sweeps on the sufficient statistics
 struct SSArgs {
     const float2* U; const float2* S;
-    const DiagDesc* desc; const int* slot;
+    const DiagDesc* desc;
+    const int* slot_pad;    // slot words, n_pad per diagonal from DiagDesc::pslot_off (padding 0)
     const float* J; const float* eta;   // eta: direction (Hessian) or LM step x (trial)
     float* part; double* part_dcost; int* status;
     int A, N, K, D, slots_max;

@@ -72,7 +72,7 @@ struct calib_ctx {
 
     // layout (depends on flags)
     std::vector<DiagDesc> desc_h;
-    std::vector<int> slot_h, slot_b_h;
+    std::vector<int> slot_h, slot_b_h, slot_pad_h;
     long long int_v = 0, int_c = 0;             // internal totals (float2)
     long long int_u = 0, int_s = 0;             // sufficient-statistics totals (float2)
     double alg_bytes[4] = {0, 0, 0, 0};         // algorithmic bytes per launch of each sweep kind
@@ -84,7 +84,7 @@ struct calib_ctx {
     int formulation = 0;  // 0 sufficient statistics, 1 direct
     bool ss_dirty = true;
     DiagDesc* desc = nullptr;
-    int *slot = nullptr, *slot_b = nullptr, *T_d = nullptr;
+    int *slot = nullptr, *slot_b = nullptr, *slot_pad = nullptr, *T_d = nullptr;
     int2* inc = nullptr;
     float* gw = nullptr;  // [A][K][N][N] Jacobi weights
     long long *vis_off_d = nullptr, *coh_off_d = nullptr;
@@ -184,7 +184,7 @@ SSArgs ss_args(calib_ctx* c, const float* J, const float* eta) {
     a.U = c->ssU;
     a.S = c->ssS;
     a.desc = c->desc;
-    a.slot = c->slot;
+    a.slot_pad = c->slot_pad;
     a.J = J;
     a.eta = eta;
     a.part = c->part;
@@ -287,6 +287,7 @@ void free_layout(calib_ctx* c) {
     cudaFree(c->desc); c->desc = nullptr;
     cudaFree(c->slot); c->slot = nullptr;
     cudaFree(c->slot_b); c->slot_b = nullptr;
+    cudaFree(c->slot_pad); c->slot_pad = nullptr;
     cudaFree(c->gw); c->gw = nullptr;
     cudaFree(c->ssU); c->ssU = nullptr;
     cudaFree(c->ssS); c->ssS = nullptr;
@@ -311,6 +312,7 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     c->desc_h.assign((size_t)A * D, DiagDesc{});
     c->slot_h.clear();
     c->slot_b_h.clear();
+    c->slot_pad_h.clear();
     long long voff = 0, coff = 0, uoff = 0, soff = 0;
     const int KK = K * (K + 1) / 2;
     int smax = 4;
@@ -335,6 +337,9 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
             }
             dd.n = n;
             dd.n_pad = (n + 3) / 4 * 4;
+            dd.pslot_off = (int)c->slot_pad_h.size();
+            c->slot_pad_h.insert(c->slot_pad_h.end(), c->slot_h.end() - n, c->slot_h.end());
+            c->slot_pad_h.resize(c->slot_pad_h.size() + (dd.n_pad - n), 0);
             dd.voff = voff;
             dd.coff = coff;
             dd.uoff = uoff;
@@ -382,6 +387,9 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     CK(dalloc(&c->desc, c->desc_h.size()));
     CK(dalloc(&c->slot, c->slot_h.size()));
     CK(dalloc(&c->slot_b, c->slot_b_h.size()));
+    CK(dalloc(&c->slot_pad, std::max<size_t>(4, c->slot_pad_h.size())));
+    if (!c->slot_pad_h.empty())
+        CK(cudaMemcpy(c->slot_pad, c->slot_pad_h.data(), c->slot_pad_h.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(dalloc(&c->gw, (size_t)A * K * N * N));
     CK(dalloc(&c->ssU, (size_t)c->int_u));
     CK(dalloc(&c->ssS, (size_t)c->int_s));

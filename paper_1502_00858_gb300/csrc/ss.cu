@@ -28,7 +28,7 @@ namespace calib {
 namespace {
 
 constexpr int NST = 2;   // one stage = one whole diagonal; one stage of prefetch hides the bulk-copy latency
-constexpr int BAR_BYTES = 64;  // barrier area, keeps the rows below 16-byte aligned
+constexpr int BAR_BYTES = 128;  // mbarriers (16 B) and the stages' diagonal descriptors; keeps what follows 16-byte aligned
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -76,17 +76,21 @@ __device__ __forceinline__ void cmac(float2& acc, float2 s, float2 q) {
     acc.x = fmaf(s.x, q.x, fmaf(-s.y, q.y, acc.x));
     acc.y = fmaf(s.x, q.y, fmaf(s.y, q.x, acc.y));
 }
+// a[0] conj(b[0]) + a[1] conj(b[1]) for two complex pairs packed as (re, im, re, im)
+__device__ __forceinline__ float2 cdot2(float4 a, float4 b) {
+    return make_float2(a.x * b.x + a.y * b.y + (a.z * b.z + a.w * b.w), a.y * b.x - a.x * b.y + (a.w * b.z - a.z * b.w));
+}
 __device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
 // value of the partner lane (lane ^ 1: the other row of the same slot)
 __device__ __forceinline__ float2 shfl2x(float2 v) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1));
 }
 
-// KB: register bucket; EXACT: K == KB, so every loop bound and packed-S index is a constant.
 // CTA holding item i of W items split into G equal contiguous ranges (start(c) = floor(c W / G)).
 __device__ __forceinline__ long long cta_of_item(long long i, long long W, long long G) { return ((i + 1) * G - 1) / W; }
 
 // KB: register bucket; EXACT: K == KB, so every loop bound and packed-S index is a constant.
+// Stage layout: [U: n_pad][K][2 rows] float4 (trial only) | [S: n_pad][KK] float2 | [slot words: n_pad] int.
 template <int KB, bool HV, bool EXACT>
 __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int stage_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -94,12 +98,14 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
     const int K = EXACT ? KB : a.K;
     const int KK = K * (K + 1) / 2;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int g = tid >> 1, rr = tid & 1;
+    const int g = tid >> 1, rr = tid & 1, ro = rr ^ 1;
     const int lane = tid & 31;
     const int KN2 = K * N * 2;  // float4 per vector: [K][N][row]
 
     unsigned char* stage = smem;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NST * stage_bytes);
+    DiagDesc* sdesc = reinterpret_cast<DiagDesc*>(smem + NST * stage_bytes + 16);  // [NST]
+    static_assert(16 + NST * sizeof(DiagDesc) <= BAR_BYTES, "barrier area too small");
     float4* Js = reinterpret_cast<float4*>(smem + NST * stage_bytes + BAR_BYTES);  // [K][N][2 rows]
     float4* Es = Js + KN2;     // eta (Hessian) or x (trial)
     float4* acc = Es + KN2;    // first-station sums
@@ -109,6 +115,7 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
     const long long W = (long long)a.A * D, G = gridDim.x;
     const long long i0 = (long long)blockIdx.x * W / G;
     const int S = (int)((long long)(blockIdx.x + 1) * W / G - i0);
+    const int ag0 = (int)(i0 / D), d0 = (int)(i0 - (long long)ag0 * D);
 
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) mbar_init(&bar[i], 1);
@@ -116,23 +123,23 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
     }
     __syncthreads();
 
-    auto desc_of = [&](int s2) -> DiagDesc {
-        const long long it = i0 + s2;
-        const long long ag = it / D;
-        return a.desc[(size_t)ag * D + (size_t)(it - ag * D)];
-    };
+    // Thread 0 issues the stages in order; (iss_ag, iss_d) is the item of the next one.
+    int iss_ag = ag0, iss_d = d0;
     auto issue = [&](int s2) {
-        const DiagDesc d2 = desc_of(s2);
+        const DiagDesc d2 = a.desc[(size_t)iss_ag * D + iss_d];
+        if (++iss_d == D) { iss_d = 0; ++iss_ag; }
         const uint32_t ub = HV ? 0u : (uint32_t)(d2.n_pad * K * 32);
         const uint32_t sb = (uint32_t)(d2.n_pad * KK * 8);
+        const uint32_t pb = (uint32_t)(d2.n_pad * 4);
         unsigned char* buf = stage + (s2 % NST) * stage_bytes;
         uint64_t* b = &bar[s2 % NST];
-        mbar_expect_tx(b, ub + sb);
+        sdesc[s2 % NST] = d2;
+        mbar_expect_tx(b, ub + sb + pb);
         if (ub) bulk_g2s(buf, a.U + d2.uoff, ub, b);
         if (sb) bulk_g2s(buf + ub, a.S + d2.soff, sb, b);
+        if (pb) bulk_g2s(buf + ub + sb, a.slot_pad + d2.pslot_off, pb, b);
     };
-    if (tid == 0)
-        for (int s2 = 0; s2 < min(NST - 1, S); ++s2) issue(s2);
+    if (tid == 0 && S > 0) issue(0);
 
     // Station sums of the finished agent -> its partial; call from uniform control flow after a barrier.
     auto flush = [&](int ag, double dc) {
@@ -155,14 +162,12 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
         }
     };
 
-    int agent = -1;
+    int agent = -1, ag = ag0, dg = d0;  // current agent with staged J / eta; item of stage s
     double dcost = 0.0;
     for (int s = 0; s < S; ++s) {
-        const long long it = i0 + s;
-        const int ag = (int)(it / D);
         if (ag != agent) {
             if (agent >= 0) {
-                __syncthreads();  // every thread is done with the previous agent's stage and sums
+                __syncthreads();  // every thread is done with the previous agent's sums
                 flush(agent, dcost);
                 dcost = 0.0;
                 __syncthreads();  // the sums are read out before they are cleared
@@ -178,13 +183,10 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
                 accs[i] = z4;
             }
         }
-        const DiagDesc dsc = desc_of(s);
-        __syncthreads();  // the buffer of stage s + NST - 1 is free; the agent's J / eta are staged
-        if (tid == 0 && s + NST - 1 < S) {
-            fence_proxy_async_smem();
-            issue(s + NST - 1);
-        }
+        if (++dg == D) { dg = 0; ++ag; }
         const bool ok = mbar_wait_bounded(&bar[s % NST], (uint32_t)((s / NST) & 1));
+        // One barrier per stage: stage s has landed everywhere, every thread is done with stage
+        // s - 1 (its buffer is free for stage s + 1), and the agent's J / eta are staged.
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicOr(a.status, STATUS_TIMEOUT);
@@ -193,55 +195,53 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
             }
             return;
         }
+        if (tid == 0 && s + 1 < S) {
+            fence_proxy_async_smem();
+            issue(s + 1);
+        }
+        const DiagDesc& dsc = sdesc[s % NST];
+        const int n = dsc.n, n_pad = dsc.n_pad;
         const unsigned char* buf = stage + (s % NST) * stage_bytes;
-        const float4* Us = reinterpret_cast<const float4*>(buf);  // [n_pad][K][2 rows] (trial)
-        const float2* Ss = reinterpret_cast<const float2*>(buf + (HV ? 0 : dsc.n_pad * K * 32)) + (size_t)g * KK;
-        const bool active = g < dsc.n;
+        const float2* Us = reinterpret_cast<const float2*>(buf);  // [n_pad][K][2][2] (trial)
+        const float2* Ss = reinterpret_cast<const float2*>(buf + (HV ? 0 : n_pad * K * 32)) + (size_t)g * KK;
+        const int* slots = reinterpret_cast<const int*>(buf + (HV ? 0 : n_pad * K * 32) + n_pad * KK * 8);
+        const bool active = g < n;
         int first = 0, second = 0;
-        // Row rr of X_k: Hessian -(S Q)_k; trial W'_k = U_k - (S P)_k - (S dP)_k. Columns 0 and 1.
-        float2 X0[KB], X1[KB];
+        // Row rr of X_k in column order (rr, 1 - rr): Hessian (S Q)_k; trial W'_k = U_k - (S P)_k - (S dP)_k.
+        float2 Xd[KB], Xo[KB];
 #pragma unroll
-        for (int k = 0; k < KB; ++k) X0[k] = X1[k] = make_float2(0.f, 0.f);
+        for (int k = 0; k < KB; ++k) Xd[k] = Xo[k] = make_float2(0.f, 0.f);
         if (active) {
-            const int sl = a.slot[dsc.slot_off + g];
+            const int sl = slots[g];
             first = sl & 0xff;
             second = (sl >> 8) & 0xff;
-            float2 Y0[HV ? 1 : KB], Y1[HV ? 1 : KB];    // trial: row rr of (S dP)_k
-            float2 dP0[HV ? 1 : KB], dP1[HV ? 1 : KB];  // trial: row rr of dP_l
+            float2 Yd[HV ? 1 : KB], Yo[HV ? 1 : KB];    // trial: row rr of (S dP)_k
+            float2 dPd[HV ? 1 : KB], dPo[HV ? 1 : KB];  // trial: row rr of dP_l
             if (!HV) {
 #pragma unroll
-                for (int k = 0; k < KB; ++k) Y0[k] = Y1[k] = dP0[k] = dP1[k] = make_float2(0.f, 0.f);
+                for (int k = 0; k < KB; ++k) Yd[k] = Yo[k] = dPd[k] = dPo[k] = make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int l = 0; l < KB; ++l) {
                 if (l >= K) continue;
-                // row rr of the first station's blocks, both rows of the second station's
+                // row rr of the first station's blocks; rows rr and 1 - rr of the second station's
                 const float4 jf = Js[(l * N + first) * 2 + rr], ef = Es[(l * N + first) * 2 + rr];
-                const float4 js0 = Js[(l * N + second) * 2 + 0], js1 = Js[(l * N + second) * 2 + 1];
-                const float4 es0 = Es[(l * N + second) * 2 + 0], es1 = Es[(l * N + second) * 2 + 1];
-                const float2 jf0 = make_float2(jf.x, jf.y), jf1 = make_float2(jf.z, jf.w);
-                const float2 ef0 = make_float2(ef.x, ef.y), ef1 = make_float2(ef.z, ef.w);
-                // (A B^H)[rr][c] = A[rr][0] conj(B[c][0]) + A[rr][1] conj(B[c][1]); B[c] = row c
-                const float2 js00 = make_float2(js0.x, js0.y), js01 = make_float2(js0.z, js0.w);
-                const float2 js10 = make_float2(js1.x, js1.y), js11 = make_float2(js1.z, js1.w);
-                const float2 es00 = make_float2(es0.x, es0.y), es01 = make_float2(es0.z, es0.w);
-                const float2 es10 = make_float2(es1.x, es1.y), es11 = make_float2(es1.z, es1.w);
-                float2 q0, q1, p0 = make_float2(0.f, 0.f), p1 = make_float2(0.f, 0.f);
-                const float2 efs0 = f2add(cmul_cb(ef0, js00), cmul_cb(ef1, js01));
-                const float2 efs1 = f2add(cmul_cb(ef0, js10), cmul_cb(ef1, js11));
-                const float2 jfe0 = f2add(cmul_cb(jf0, es00), cmul_cb(jf1, es01));
-                const float2 jfe1 = f2add(cmul_cb(jf0, es10), cmul_cb(jf1, es11));
+                const float4 jsd = Js[(l * N + second) * 2 + rr], jso = Js[(l * N + second) * 2 + ro];
+                const float4 esd = Es[(l * N + second) * 2 + rr], eso = Es[(l * N + second) * 2 + ro];
+                // (A B^H)[rr][c] = A[rr][0] conj(B[c][0]) + A[rr][1] conj(B[c][1]), c = rr (d) and 1 - rr (o)
+                const float2 efsd = cdot2(ef, jsd), efso = cdot2(ef, jso);
+                const float2 jfed = cdot2(jf, esd), jfeo = cdot2(jf, eso);
+                float2 qd, qo, pd = make_float2(0.f, 0.f), po = make_float2(0.f, 0.f);
                 if (HV) {
-                    q0 = f2add(efs0, jfe0);  // Q_l = eta_f J_s^H + J_f eta_s^H
-                    q1 = f2add(efs1, jfe1);
+                    qd = f2add(efsd, jfed);  // Q_l = eta_f J_s^H + J_f eta_s^H
+                    qo = f2add(efso, jfeo);
                 } else {
-                    q0 = f2add(cmul_cb(jf0, js00), cmul_cb(jf1, js01));  // P_l = J_f J_s^H
-                    q1 = f2add(cmul_cb(jf0, js10), cmul_cb(jf1, js11));
-                    // dP_l = x_f J_s^H + J_f x_s^H + x_f x_s^H
-                    p0 = f2add(f2add(efs0, jfe0), f2add(cmul_cb(ef0, es00), cmul_cb(ef1, es01)));
-                    p1 = f2add(f2add(efs1, jfe1), f2add(cmul_cb(ef0, es10), cmul_cb(ef1, es11)));
-                    dP0[l] = p0;
-                    dP1[l] = p1;
+                    qd = cdot2(jf, jsd);  // P_l = J_f J_s^H
+                    qo = cdot2(jf, jso);
+                    pd = f2add(f2add(efsd, jfed), cdot2(ef, esd));  // dP_l = x_f J_s^H + J_f x_s^H + x_f x_s^H
+                    po = f2add(f2add(efso, jfeo), cdot2(ef, eso));
+                    dPd[l] = pd;
+                    dPo[l] = po;
                 }
 #pragma unroll
                 for (int k = 0; k < KB; ++k) {
@@ -250,66 +250,62 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
                     const int lo = k < l ? k : l, hi = k < l ? l : k;
                     float2 skl = Ss[lo * K - lo * (lo - 1) / 2 + (hi - lo)];
                     if (k > l) skl.y = -skl.y;
-                    cmac(X0[k], skl, q0);
-                    cmac(X1[k], skl, q1);
+                    cmac(Xd[k], skl, qd);
+                    cmac(Xo[k], skl, qo);
                     if (!HV) {
-                        cmac(Y0[k], skl, p0);
-                        cmac(Y1[k], skl, p1);
+                        cmac(Yd[k], skl, pd);
+                        cmac(Yo[k], skl, po);
                     }
                 }
             }
-            if (HV) {
-#pragma unroll
-                for (int k = 0; k < KB; ++k) {
-                    X0[k] = make_float2(-X0[k].x, -X0[k].y);
-                    X1[k] = make_float2(-X1[k].x, -X1[k].y);
-                }
-            } else {
+            if (!HV) {
                 float dcf = 0.f;
 #pragma unroll
                 for (int k = 0; k < KB; ++k) {
                     if (k >= K) continue;
-                    const float4 u = Us[((size_t)g * K + k) * 2 + rr];
-                    const float2 W0 = make_float2(u.x - X0[k].x, u.y - X0[k].y);  // W_k at J
-                    const float2 W1 = make_float2(u.z - X1[k].x, u.w - X1[k].y);
+                    const float2* u = Us + (((size_t)g * K + k) * 2 + rr) * 2;
+                    const float2 Wd = f2sub(u[rr], Xd[k]);  // W_k at J
+                    const float2 Wo = f2sub(u[ro], Xo[k]);
                     // decrease: Re[conj(dP_k) (2 W_k - (S dP)_k)], this row
-                    dcf = fmaf(dP0[k].x, 2.f * W0.x - Y0[k].x, fmaf(dP0[k].y, 2.f * W0.y - Y0[k].y, dcf));
-                    dcf = fmaf(dP1[k].x, 2.f * W1.x - Y1[k].x, fmaf(dP1[k].y, 2.f * W1.y - Y1[k].y, dcf));
-                    X0[k] = f2sub(W0, Y0[k]);  // W'_k at J' = J + x
-                    X1[k] = f2sub(W1, Y1[k]);
+                    dcf = fmaf(dPd[k].x, 2.f * Wd.x - Yd[k].x, fmaf(dPd[k].y, 2.f * Wd.y - Yd[k].y, dcf));
+                    dcf = fmaf(dPo[k].x, 2.f * Wo.x - Yo[k].x, fmaf(dPo[k].y, 2.f * Wo.y - Yo[k].y, dcf));
+                    Xd[k] = f2sub(Wd, Yd[k]);  // W'_k at J' = J + x
+                    Xo[k] = f2sub(Wo, Yo[k]);
                 }
                 dcost += (double)dcf;
             }
         }
-        // First station: -= row rr of X_k J'_s (J' = J + x in the trial pass).
-        // Second station: -= row rr of X_k^H J'_f = conj(X[0][rr]) J'_f[0][.] + conj(X[1][rr]) J'_f[1][.].
+        // Station terms, row rr (J' = J + x in the trial pass; Hessian: +, trial: -):
+        //   first:  (X J'_s)[rr][.]   = X[rr][rr] J'_s[rr][.] + X[rr][1-rr] J'_s[1-rr][.]
+        //   second: (X^H J'_f)[rr][.] = conj(X[rr][rr]) J'_f[rr][.] + conj(X[1-rr][rr]) J'_f[1-rr][.]
+        // X[1-rr][rr] is the partner lane's Xo.
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
             if (k >= K) continue;
-            const float2 send = rr == 0 ? X1[k] : X0[k];  // X[rr][1-rr], wanted by the partner
-            const float2 oth = shfl2x(send);              // X[1-rr][rr]
+            const float2 xp = shfl2x(Xo[k]);
             if (!active) continue;
-            const float2 own = rr == 0 ? X0[k] : X1[k];   // X[rr][rr]
-            const float2 xc0 = rr == 0 ? own : oth, xc1 = rr == 0 ? oth : own;  // X[0][rr], X[1][rr]
-            float4 s0 = Js[(k * N + second) * 2 + 0], s1 = Js[(k * N + second) * 2 + 1];
-            float4 f0 = Js[(k * N + first) * 2 + 0], f1 = Js[(k * N + first) * 2 + 1];
+            float4 sd = Js[(k * N + second) * 2 + rr], so = Js[(k * N + second) * 2 + ro];
+            float4 fd = Js[(k * N + first) * 2 + rr], fo = Js[(k * N + first) * 2 + ro];
             if (!HV) {
-                s0 = f4add(s0, Es[(k * N + second) * 2 + 0]);
-                s1 = f4add(s1, Es[(k * N + second) * 2 + 1]);
-                f0 = f4add(f0, Es[(k * N + first) * 2 + 0]);
-                f1 = f4add(f1, Es[(k * N + first) * 2 + 1]);
+                sd = f4add(sd, Es[(k * N + second) * 2 + rr]);
+                so = f4add(so, Es[(k * N + second) * 2 + ro]);
+                fd = f4add(fd, Es[(k * N + first) * 2 + rr]);
+                fo = f4add(fo, Es[(k * N + first) * 2 + ro]);
             }
-            // (X J'_s)[rr][c] = X[rr][0] J'_s[0][c] + X[rr][1] J'_s[1][c]
-            const float2 v0 = f2add(cmul(X0[k], make_float2(s0.x, s0.y)), cmul(X1[k], make_float2(s1.x, s1.y)));
-            const float2 v1 = f2add(cmul(X0[k], make_float2(s0.z, s0.w)), cmul(X1[k], make_float2(s1.z, s1.w)));
+            const float2 v0 = f2add(cmul(Xd[k], make_float2(sd.x, sd.y)), cmul(Xo[k], make_float2(so.x, so.y)));
+            const float2 v1 = f2add(cmul(Xd[k], make_float2(sd.z, sd.w)), cmul(Xo[k], make_float2(so.z, so.w)));
+            const float2 w0 = f2add(cmul_ca(Xd[k], make_float2(fd.x, fd.y)), cmul_ca(xp, make_float2(fo.x, fo.y)));
+            const float2 w1 = f2add(cmul_ca(Xd[k], make_float2(fd.z, fd.w)), cmul_ca(xp, make_float2(fo.z, fo.w)));
             float4* d1 = acc + (k * N + first) * 2 + rr;
-            float4 t1 = *d1;
-            *d1 = make_float4(t1.x - v0.x, t1.y - v0.y, t1.z - v1.x, t1.w - v1.y);
-            const float2 w0 = f2add(cmul_ca(xc0, make_float2(f0.x, f0.y)), cmul_ca(xc1, make_float2(f1.x, f1.y)));
-            const float2 w1 = f2add(cmul_ca(xc0, make_float2(f0.z, f0.w)), cmul_ca(xc1, make_float2(f1.z, f1.w)));
             float4* d2 = accs + (k * N + second) * 2 + rr;
-            float4 t2 = *d2;
-            *d2 = make_float4(t2.x - w0.x, t2.y - w0.y, t2.z - w1.x, t2.w - w1.y);
+            const float4 t1 = *d1, t2 = *d2;
+            if (HV) {
+                *d1 = make_float4(t1.x + v0.x, t1.y + v0.y, t1.z + v1.x, t1.w + v1.y);
+                *d2 = make_float4(t2.x + w0.x, t2.y + w0.y, t2.z + w1.x, t2.w + w1.y);
+            } else {
+                *d1 = make_float4(t1.x - v0.x, t1.y - v0.y, t1.z - v1.x, t1.w - v1.y);
+                *d2 = make_float4(t2.x - w0.x, t2.y - w0.y, t2.z - w1.x, t2.w - w1.y);
+            }
         }
     }
     if (agent >= 0) {
@@ -373,7 +369,7 @@ cudaError_t prepare_ss_kernels() {
 
 size_t ss_sweep_smem_bytes(int N, int K, int slots_max, bool hessvec, int* stage_bytes) {
     const int KK = K * (K + 1) / 2;
-    const int per_slot = (hessvec ? 0 : K * 32) + KK * 8;
+    const int per_slot = (hessvec ? 0 : K * 32) + KK * 8 + 4;
     const int sb = ((slots_max * per_slot + 127) / 128) * 128;
     if (stage_bytes) *stage_bytes = sb;
     return (size_t)NST * sb + BAR_BYTES + (size_t)4 * K * N * 32 + 32 * 8;
