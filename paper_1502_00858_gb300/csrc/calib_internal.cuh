@@ -21,6 +21,10 @@
 // is conjugate-transposed (V) / conjugated (c) on ingestion, so kernels never see orientation.
 //   V block of (agent, diagonal): [T_a][n_pad][4] float2 (32 B per slot and sample)
 //   C block of (agent, diagonal): [T_a][n_pad][K] float2
+// The sufficient statistics use the full circulant layout instead (no compaction): diagonal d of
+// agent a holds NP = roundup(N, 4) slot positions, position i = the pair (i, (i+d) mod N)
+// (i < N, or i < N/2 on the diagonal d = N/2), zero statistics where the baseline is flagged:
+//   U[((a*D + d-1)*NP + i)*K*4 ...]  [K][2][2] float2,   S[((a*D + d-1)*NP + i)*KK ...]  packed.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -49,7 +53,7 @@ struct DiagDesc {     // one per (agent, diagonal)
     int slot_off;     // global index of the first slot of this diagonal in the slot arrays
     int n;            // active (unflagged) slots
     int n_pad;        // padded slot count (multiple of 4, >= n)
-    int pslot_off;    // index of this diagonal's n_pad slot words in the padded slot array (multiple of 4)
+    int pad_;
 };
 
 struct AgentState {   // per-agent scalars
@@ -158,23 +162,22 @@ cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s);
 cudaError_t launch_gram_weights(const float2* C, const DiagDesc* desc, const int* slot, const int* T, float* gw,
                                 int A, int D, int K, int N, cudaStream_t s);
 cudaError_t launch_check_finite(const float* x, long long n, int* status, cudaStream_t s);
+// Statistics into the full circulant layout (zero where flagged; clears U and S first).
 cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc,
-                            const int* T, int A, int D, int K, cudaStream_t s);
+                            const int* slot, const int* T, int A, int D, int K, int N, cudaStream_t s);
 
 // ---- launchers (ss.cu): sweeps on the sufficient statistics
 struct SSArgs {
-    const float2* U; const float2* S;
-    const DiagDesc* desc;
-    const int* slot_pad;    // slot words, n_pad per diagonal from DiagDesc::pslot_off (padding 0)
+    const float2* U; const float2* S;    // full circulant layout, NP positions per diagonal
     const float* J; const float* eta;   // eta: direction (Hessian) or LM step x (trial)
     float* part; double* part_dcost; int* status;
-    int A, N, K, D, slots_max;
+    int A, N, K, D, NP;
     int part_stride;   // pieces per agent in part / part_dcost (>= the CTAs meeting any one agent)
 };
 // grid CTAs split the A*D (agent, diagonal) items into equal contiguous ranges; 1 <= grid <= A*D.
 cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, int grid, cudaStream_t s);
-size_t ss_sweep_smem_bytes(int N, int K, int slots_max, bool hessvec, int* stage_bytes);
-int ss_sweep_threads(int slots_max);
+size_t ss_sweep_smem_bytes(int N, int K, bool hessvec, int* stage_bytes);
+int ss_sweep_threads(int N);
 cudaError_t prepare_ss_kernels();
 
 // One-time kernel attribute set-up (dynamic shared memory limits); call before any capture.

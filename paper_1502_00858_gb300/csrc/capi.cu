@@ -72,7 +72,7 @@ struct calib_ctx {
 
     // layout (depends on flags)
     std::vector<DiagDesc> desc_h;
-    std::vector<int> slot_h, slot_b_h, slot_pad_h;
+    std::vector<int> slot_h, slot_b_h;
     long long int_v = 0, int_c = 0;             // internal totals (float2)
     long long int_u = 0, int_s = 0;             // sufficient-statistics totals (float2)
     double alg_bytes[4] = {0, 0, 0, 0};         // algorithmic bytes per launch of each sweep kind
@@ -84,7 +84,7 @@ struct calib_ctx {
     int formulation = 0;  // 0 sufficient statistics, 1 direct
     bool ss_dirty = true;
     DiagDesc* desc = nullptr;
-    int *slot = nullptr, *slot_b = nullptr, *slot_pad = nullptr, *T_d = nullptr;
+    int *slot = nullptr, *slot_b = nullptr, *T_d = nullptr;
     int2* inc = nullptr;
     float* gw = nullptr;  // [A][K][N][N] Jacobi weights
     long long *vis_off_d = nullptr, *coh_off_d = nullptr;
@@ -183,8 +183,6 @@ SSArgs ss_args(calib_ctx* c, const float* J, const float* eta) {
     SSArgs a{};
     a.U = c->ssU;
     a.S = c->ssS;
-    a.desc = c->desc;
-    a.slot_pad = c->slot_pad;
     a.J = J;
     a.eta = eta;
     a.part = c->part;
@@ -194,7 +192,7 @@ SSArgs ss_args(calib_ctx* c, const float* J, const float* eta) {
     a.N = c->N;
     a.K = c->K;
     a.D = c->D;
-    a.slots_max = c->slots_max;
+    a.NP = (c->N + 3) / 4 * 4;
     a.part_stride = c->stride_ss;
     return a;
 }
@@ -287,7 +285,6 @@ void free_layout(calib_ctx* c) {
     cudaFree(c->desc); c->desc = nullptr;
     cudaFree(c->slot); c->slot = nullptr;
     cudaFree(c->slot_b); c->slot_b = nullptr;
-    cudaFree(c->slot_pad); c->slot_pad = nullptr;
     cudaFree(c->gw); c->gw = nullptr;
     cudaFree(c->ssU); c->ssU = nullptr;
     cudaFree(c->ssS); c->ssS = nullptr;
@@ -312,7 +309,6 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     c->desc_h.assign((size_t)A * D, DiagDesc{});
     c->slot_h.clear();
     c->slot_b_h.clear();
-    c->slot_pad_h.clear();
     long long voff = 0, coff = 0, uoff = 0, soff = 0;
     const int KK = K * (K + 1) / 2;
     int smax = 4;
@@ -337,9 +333,6 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
             }
             dd.n = n;
             dd.n_pad = (n + 3) / 4 * 4;
-            dd.pslot_off = (int)c->slot_pad_h.size();
-            c->slot_pad_h.insert(c->slot_pad_h.end(), c->slot_h.end() - n, c->slot_h.end());
-            c->slot_pad_h.resize(c->slot_pad_h.size() + (dd.n_pad - n), 0);
             dd.voff = voff;
             dd.coff = coff;
             dd.uoff = uoff;
@@ -365,8 +358,12 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     }
     c->int_v = voff;
     c->int_c = coff;
-    c->int_u = uoff;
-    c->int_s = soff;
+    // sufficient statistics: full circulant layout, NP positions per (agent, diagonal)
+    const long long NP = (N + 3) / 4 * 4;
+    c->int_u = (long long)A * D * NP * K * 4;
+    c->int_s = (long long)A * D * NP * KK;
+    (void)uoff;
+    (void)soff;
     c->slots_max = smax;
     c->alg_bytes[0] = alg_res;
     c->alg_bytes[1] = alg_hv;
@@ -378,7 +375,7 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     if (sweep_threads(smax) > 512) return fail(CALIB_EINVAL, "too many stations for one CTA per diagonal");
     if ((size_t)3 * 24 * 1024 + sweep_smem_bytes(N, K, true) + 4096 > 200 * 1024)
         return fail(CALIB_EINVAL, "N*K too large for the sweep kernels' shared memory");
-    if (c->formulation == 0 && ss_sweep_smem_bytes(N, K, smax, false, nullptr) > 200 * 1024)
+    if (c->formulation == 0 && ss_sweep_smem_bytes(N, K, false, nullptr) > 200 * 1024)
         return fail(CALIB_EINVAL, "N*K too large for the statistics sweeps' shared memory; use CALIB_FORM_DIRECT");
 
     free_layout(c);
@@ -387,9 +384,6 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     CK(dalloc(&c->desc, c->desc_h.size()));
     CK(dalloc(&c->slot, c->slot_h.size()));
     CK(dalloc(&c->slot_b, c->slot_b_h.size()));
-    CK(dalloc(&c->slot_pad, std::max<size_t>(4, c->slot_pad_h.size())));
-    if (!c->slot_pad_h.empty())
-        CK(cudaMemcpy(c->slot_pad, c->slot_pad_h.data(), c->slot_pad_h.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(dalloc(&c->gw, (size_t)A * K * N * N));
     CK(dalloc(&c->ssU, (size_t)c->int_u));
     CK(dalloc(&c->ssS, (size_t)c->int_s));
@@ -969,7 +963,7 @@ int calib_admm_iter(calib_ctx* c, int n_iters, calib_stats* hist) {
     CK(cudaMemsetAsync(c->iter_counter, 0, sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     if (c->formulation == 0 && c->ss_dirty) {
-        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->T_d, c->A, c->D, c->K, c->stream));
+        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->slot, c->T_d, c->A, c->D, c->K, c->N, c->stream));
         c->launches += 1;
         c->ss_dirty = false;
     }
@@ -1207,7 +1201,7 @@ int calib_autotune(calib_ctx* c, int* split, int cap, int* cand, double* ms_per_
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "set visibilities and coherencies first");
     if (c->formulation == 0 && c->ss_dirty) {
-        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->T_d, c->A, c->D, c->K, c->stream));
+        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->slot, c->T_d, c->A, c->D, c->K, c->N, c->stream));
         c->launches += 1;
         c->ss_dirty = false;
     }

@@ -165,15 +165,20 @@ __global__ void k_gram_weights(const float2* C, const DiagDesc* desc, const int*
 
 // Sufficient statistics per (agent, diagonal): thread (slot g, entry e) accumulates
 // U_k[e] = sum_t conj(c_tk) V_t[e] for all k, and its share of the packed S_kl = sum_t conj(c_tk) c_tl.
+// Written into the full circulant layout: compacted slot g goes to position i = its first station;
+// positions of flagged baselines keep the zeros the launcher cleared them to.
 __global__ void __launch_bounds__(256) k_ss_stats(const float2* V, const float2* C, float2* U, float2* S,
-                                                  const DiagDesc* desc, const int* T, int D, int K) {
+                                                  const DiagDesc* desc, const int* slot, const int* T, int D,
+                                                  int K, int NP) {
     const int d = blockIdx.x, agent = blockIdx.y;
     const DiagDesc dsc = desc[(size_t)agent * D + d];
     const int Ta = T[agent];
     const int KK = K * (K + 1) / 2;
-    for (int base = 0; base < dsc.n_pad; base += blockDim.x / 4) {
+    const size_t blk = ((size_t)agent * D + d) * NP;  // first position of this (agent, diagonal)
+    for (int base = 0; base < dsc.n; base += blockDim.x / 4) {
         const int g = base + (threadIdx.x >> 2), e = threadIdx.x & 3;
-        if (g >= dsc.n_pad) continue;
+        if (g >= dsc.n) continue;
+        const size_t pos = blk + (slot[dsc.slot_off + g] & 0xff);
         float2 u[MAX_K];
         for (int k = 0; k < K; ++k) u[k] = make_float2(0.f, 0.f);
         for (int t = 0; t < Ta; ++t) {
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(256) k_ss_stats(const float2* V, const float2*
                 u[k].y = fmaf(c.x, v.y, fmaf(-c.y, v.x, u[k].y));
             }
         }
-        float2* uo = U + dsc.uoff + (size_t)g * K * 4;
+        float2* uo = U + pos * K * 4;
         for (int k = 0; k < K; ++k) uo[k * 4 + e] = u[k];
         // packed S entries idx = e, e + 4, ...
         for (int idx = e; idx < KK; idx += 4) {
@@ -199,7 +204,7 @@ __global__ void __launch_bounds__(256) k_ss_stats(const float2* V, const float2*
                 sr = fmaf(ck.x, cl.x, fmaf(ck.y, cl.y, sr));   // conj(c_k) c_l
                 si = fmaf(ck.x, cl.y, fmaf(-ck.y, cl.x, si));
             }
-            S[dsc.soff + (size_t)g * KK + idx] = make_float2(sr, si);
+            S[pos * KK + idx] = make_float2(sr, si);
         }
     }
 }
@@ -243,9 +248,14 @@ cudaError_t launch_gram_weights(const float2* C, const DiagDesc* desc, const int
     return cudaGetLastError();
 }
 cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc,
-                            const int* T, int A, int D, int K, cudaStream_t s) {
+                            const int* slot, const int* T, int A, int D, int K, int N, cudaStream_t s) {
+    const int NP = (N + 3) / 4 * 4, KK = K * (K + 1) / 2;
+    const size_t pos = (size_t)A * D * NP;
+    cudaError_t e = cudaMemsetAsync(U, 0, pos * K * 4 * sizeof(float2), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, pos * KK * sizeof(float2), s);
+    if (e != cudaSuccess) return e;
     dim3 grid(D, A);
-    k_ss_stats<<<grid, 256, 0, s>>>(V, C, U, S, desc, T, D, K);
+    k_ss_stats<<<grid, 256, 0, s>>>(V, C, U, S, desc, slot, T, D, K, NP);
     return cudaGetLastError();
 }
 

@@ -12,23 +12,26 @@
 //
 // Work split: the A*D (agent, circulant diagonal) items are cut into gridDim.x equal contiguous
 // ranges, one per CTA, and the grid is a multiple of the SM count, so every SM gets the same work
-// and there is no partial last wave. A CTA stages J and eta (or x) of its current agent in shared
-// memory, streams the per-slot statistics of one diagonal per stage through a cp.async.bulk ring
-// (mbarrier, bounded waits), and writes its station sums as one partial per (agent, piece) when the
-// agent changes; piece = the CTA's index among the CTAs whose range meets that agent.
+// and there is no partial last wave. The statistics are in the full circulant layout (slot i of
+// diagonal d is the pair (i, (i+d) mod N), zero statistics where flagged), so thread pair g owns
+// station g as the first station of its slot in every diagonal: it keeps that station's rows of
+// J and eta (or x) and its first-station sums in registers for the whole agent, and only the
+// second station (g+d) mod N goes through shared memory. A CTA stages J and eta of its current
+// agent, streams the per-slot statistics of one diagonal per stage through a cp.async.bulk ring
+// (mbarrier, bounded waits), and writes the station sums as one partial per (agent, piece) when
+// the agent changes; piece = the CTA's index among the CTAs whose range meets that agent.
 // Two threads per slot, one per row of the 2x2 blocks: thread rr forms row rr of Q_l (or P_l and
-// dP_l), of the S-weighted sums X_k and of the first station's term X_k J_s. The second station's
-// term X_k^H J_f needs column rr of X_k, whose other entry comes from the partner lane. Within a
-// diagonal every station is the first element of at most one slot and the second of at most one,
-// and first- and second-station sums are kept in separate arrays, so the shared-memory updates of a
-// diagonal are conflict-free and need no barrier between the two (no atomics).
+// dP_l), of the S-weighted sums X_k and of both station terms; the second station's term
+// X_k^H J_f needs column rr of X_k, whose other entry comes from the partner lane. Within a
+// diagonal every station is the second element of exactly one slot, so the shared-memory updates
+// of a diagonal are conflict-free (no atomics).
 #include "calib_internal.cuh"
 
 namespace calib {
 namespace {
 
 constexpr int NST = 2;   // one stage = one whole diagonal; one stage of prefetch hides the bulk-copy latency
-constexpr int BAR_BYTES = 128;  // mbarriers (16 B) and the stages' diagonal descriptors; keeps what follows 16-byte aligned
+constexpr int BAR_BYTES = 64;  // barrier area, keeps what follows 16-byte aligned
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -90,32 +93,34 @@ __device__ __forceinline__ float2 shfl2x(float2 v) {
 __device__ __forceinline__ long long cta_of_item(long long i, long long W, long long G) { return ((i + 1) * G - 1) / W; }
 
 // KB: register bucket; EXACT: K == KB, so every loop bound and packed-S index is a constant.
-// Stage layout: [U: n_pad][K][2 rows] float4 (trial only) | [S: n_pad][KK] float2 | [slot words: n_pad] int.
-template <int KB, bool HV, bool EXACT>
-__global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int stage_bytes) {
+// SMALL: at most 128 threads (N <= 64). Register budgets: the Hessian pass fits 128 registers (4 CTAs
+// of 128 threads per SM); the trial pass holds three more per-direction arrays and gets 168 with
+// 128-thread CTAs (3 per SM, as many as its shared memory allows).
+// Stage layout: [U: NP][K][2 rows] float4 (trial only) | [S: NP][KK] float2.
+template <int KB, bool HV, bool EXACT, bool SMALL>
+__global__ void __launch_bounds__((!HV && SMALL) ? 128 : 256, HV ? 2 : (SMALL ? 3 : 1))
+    k_ss_sweep(const SSArgs a, const int stage_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
-    const int N = a.N, D = a.D;
+    const int N = a.N, D = a.D, NP = a.NP;
     const int K = EXACT ? KB : a.K;
     const int KK = K * (K + 1) / 2;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int g = tid >> 1, rr = tid & 1, ro = rr ^ 1;
     const int lane = tid & 31;
     const int KN2 = K * N * 2;  // float4 per vector: [K][N][row]
+    const bool own = g < N;     // this thread pair owns station g
 
     unsigned char* stage = smem;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NST * stage_bytes);
-    DiagDesc* sdesc = reinterpret_cast<DiagDesc*>(smem + NST * stage_bytes + 16);  // [NST]
-    static_assert(16 + NST * sizeof(DiagDesc) <= BAR_BYTES, "barrier area too small");
     float4* Js = reinterpret_cast<float4*>(smem + NST * stage_bytes + BAR_BYTES);  // [K][N][2 rows]
     float4* Es = Js + KN2;     // eta (Hessian) or x (trial)
-    float4* acc = Es + KN2;    // first-station sums
-    float4* accs = acc + KN2;  // second-station sums
+    float4* accs = Es + KN2;   // second-station sums
     double* red = reinterpret_cast<double*>(accs + KN2);  // [32]
 
     const long long W = (long long)a.A * D, G = gridDim.x;
     const long long i0 = (long long)blockIdx.x * W / G;
     const int S = (int)((long long)(blockIdx.x + 1) * W / G - i0);
-    const int ag0 = (int)(i0 / D), d0 = (int)(i0 - (long long)ag0 * D);
+    const int ag0 = (int)(i0 / D), d0 = (int)(i0 - (long long)ag0 * D);  // d0: 0-based diagonal
 
     if (tid == 0) {
         for (int i = 0; i < NST; ++i) mbar_init(&bar[i], 1);
@@ -126,29 +131,38 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
     // Thread 0 issues the stages in order; (iss_ag, iss_d) is the item of the next one.
     int iss_ag = ag0, iss_d = d0;
     auto issue = [&](int s2) {
-        const DiagDesc d2 = a.desc[(size_t)iss_ag * D + iss_d];
+        const size_t blk = ((size_t)iss_ag * D + iss_d) * NP;
+        const int n = (2 * (iss_d + 1) == N) ? N / 2 : N;
+        const int n4 = (n + 3) & ~3;
         if (++iss_d == D) { iss_d = 0; ++iss_ag; }
-        const uint32_t ub = HV ? 0u : (uint32_t)(d2.n_pad * K * 32);
-        const uint32_t sb = (uint32_t)(d2.n_pad * KK * 8);
-        const uint32_t pb = (uint32_t)(d2.n_pad * 4);
+        const uint32_t ub = HV ? 0u : (uint32_t)(n4 * K * 32);
+        const uint32_t sb = (uint32_t)(n4 * KK * 8);
         unsigned char* buf = stage + (s2 % NST) * stage_bytes;
         uint64_t* b = &bar[s2 % NST];
-        sdesc[s2 % NST] = d2;
-        mbar_expect_tx(b, ub + sb + pb);
-        if (ub) bulk_g2s(buf, a.U + d2.uoff, ub, b);
-        if (sb) bulk_g2s(buf + ub, a.S + d2.soff, sb, b);
-        if (pb) bulk_g2s(buf + ub + sb, a.slot_pad + d2.pslot_off, pb, b);
+        mbar_expect_tx(b, ub + sb);
+        if (!HV) bulk_g2s(buf, a.U + blk * K * 4, ub, b);
+        bulk_g2s(buf + ub, a.S + blk * KK, sb, b);
     };
     if (tid == 0 && S > 0) issue(0);
+
+    float4 Jf[KB], Ef[KB], A1[KB];  // rows rr of station g's J and eta / x; its first-station sums
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < KB; ++k) Jf[k] = Ef[k] = A1[k] = z4;
 
     // Station sums of the finished agent -> its partial; call from uniform control flow after a barrier.
     auto flush = [&](int ag, double dc) {
         const long long piece = blockIdx.x - cta_of_item((long long)ag * D, W, G);
         const size_t slot_p = (size_t)ag * a.part_stride + (size_t)piece;
         float4* out = reinterpret_cast<float4*>(a.part) + slot_p * KN2;
-        for (int i = tid; i < KN2; i += nthr) {
-            const float4 u = acc[i], w = accs[i];
-            out[i] = make_float4(u.x + w.x, u.y + w.y, u.z + w.z, u.w + w.w);
+        if (own) {
+#pragma unroll
+            for (int k = 0; k < KB; ++k) {
+                if (k >= K) continue;
+                const int i = (k * N + g) * 2 + rr;
+                const float4 w = accs[i];
+                out[i] = make_float4(A1[k].x + w.x, A1[k].y + w.y, A1[k].z + w.z, A1[k].w + w.w);
+            }
         }
         if (!HV) {
             for (int o = 16; o > 0; o >>= 1) dc += __shfl_down_sync(0xffffffffu, dc, o);
@@ -163,6 +177,7 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
     };
 
     int agent = -1, ag = ag0, dg = d0;  // current agent with staged J / eta; item of stage s
+    bool fresh = false;
     double dcost = 0.0;
     for (int s = 0; s < S; ++s) {
         if (ag != agent) {
@@ -173,16 +188,16 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
                 __syncthreads();  // the sums are read out before they are cleared
             }
             agent = ag;
+            fresh = true;
             const float4* Jg = reinterpret_cast<const float4*>(a.J) + (size_t)ag * KN2;
             const float4* Eg = reinterpret_cast<const float4*>(a.eta) + (size_t)ag * KN2;
-            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int i = tid; i < KN2; i += nthr) {
                 Js[i] = __ldg(Jg + i);
                 Es[i] = __ldg(Eg + i);
-                acc[i] = z4;
                 accs[i] = z4;
             }
         }
+        const int d = dg + 1;  // circulant diagonal of this stage
         if (++dg == D) { dg = 0; ++ag; }
         const bool ok = mbar_wait_bounded(&bar[s % NST], (uint32_t)((s / NST) & 1));
         // One barrier per stage: stage s has landed everywhere, every thread is done with stage
@@ -199,22 +214,30 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
             fence_proxy_async_smem();
             issue(s + 1);
         }
-        const DiagDesc& dsc = sdesc[s % NST];
-        const int n = dsc.n, n_pad = dsc.n_pad;
+        if (fresh) {  // station g's rows of the new agent
+            fresh = false;
+            if (own) {
+#pragma unroll
+                for (int k = 0; k < KB; ++k) {
+                    if (k >= K) continue;
+                    Jf[k] = Js[(k * N + g) * 2 + rr];
+                    Ef[k] = Es[(k * N + g) * 2 + rr];
+                    A1[k] = z4;
+                }
+            }
+        }
+        const int n = (2 * d == N) ? N / 2 : N;
+        const int n4 = (n + 3) & ~3;
         const unsigned char* buf = stage + (s % NST) * stage_bytes;
-        const float2* Us = reinterpret_cast<const float2*>(buf);  // [n_pad][K][2][2] (trial)
-        const float2* Ss = reinterpret_cast<const float2*>(buf + (HV ? 0 : n_pad * K * 32)) + (size_t)g * KK;
-        const int* slots = reinterpret_cast<const int*>(buf + (HV ? 0 : n_pad * K * 32) + n_pad * KK * 8);
+        const float2* Us = reinterpret_cast<const float2*>(buf);  // [n4][K][2][2] (trial)
+        const float2* Ss = reinterpret_cast<const float2*>(buf + (HV ? 0 : n4 * K * 32)) + (size_t)g * KK;
         const bool active = g < n;
-        int first = 0, second = 0;
+        const int second = (g + d < N) ? g + d : g + d - N;
         // Row rr of X_k in column order (rr, 1 - rr): Hessian (S Q)_k; trial W'_k = U_k - (S P)_k - (S dP)_k.
         float2 Xd[KB], Xo[KB];
 #pragma unroll
         for (int k = 0; k < KB; ++k) Xd[k] = Xo[k] = make_float2(0.f, 0.f);
         if (active) {
-            const int sl = slots[g];
-            first = sl & 0xff;
-            second = (sl >> 8) & 0xff;
             float2 Yd[HV ? 1 : KB], Yo[HV ? 1 : KB];    // trial: row rr of (S dP)_k
             float2 dPd[HV ? 1 : KB], dPo[HV ? 1 : KB];  // trial: row rr of dP_l
             if (!HV) {
@@ -224,22 +247,21 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
 #pragma unroll
             for (int l = 0; l < KB; ++l) {
                 if (l >= K) continue;
-                // row rr of the first station's blocks; rows rr and 1 - rr of the second station's
-                const float4 jf = Js[(l * N + first) * 2 + rr], ef = Es[(l * N + first) * 2 + rr];
+                // rows rr and 1 - rr of the second station's blocks
                 const float4 jsd = Js[(l * N + second) * 2 + rr], jso = Js[(l * N + second) * 2 + ro];
                 const float4 esd = Es[(l * N + second) * 2 + rr], eso = Es[(l * N + second) * 2 + ro];
                 // (A B^H)[rr][c] = A[rr][0] conj(B[c][0]) + A[rr][1] conj(B[c][1]), c = rr (d) and 1 - rr (o)
-                const float2 efsd = cdot2(ef, jsd), efso = cdot2(ef, jso);
-                const float2 jfed = cdot2(jf, esd), jfeo = cdot2(jf, eso);
+                const float2 efsd = cdot2(Ef[l], jsd), efso = cdot2(Ef[l], jso);
+                const float2 jfed = cdot2(Jf[l], esd), jfeo = cdot2(Jf[l], eso);
                 float2 qd, qo, pd = make_float2(0.f, 0.f), po = make_float2(0.f, 0.f);
                 if (HV) {
                     qd = f2add(efsd, jfed);  // Q_l = eta_f J_s^H + J_f eta_s^H
                     qo = f2add(efso, jfeo);
                 } else {
-                    qd = cdot2(jf, jsd);  // P_l = J_f J_s^H
-                    qo = cdot2(jf, jso);
-                    pd = f2add(f2add(efsd, jfed), cdot2(ef, esd));  // dP_l = x_f J_s^H + J_f x_s^H + x_f x_s^H
-                    po = f2add(f2add(efso, jfeo), cdot2(ef, eso));
+                    qd = cdot2(Jf[l], jsd);  // P_l = J_f J_s^H
+                    qo = cdot2(Jf[l], jso);
+                    pd = f2add(f2add(efsd, jfed), cdot2(Ef[l], esd));  // dP_l = x_f J_s^H + J_f x_s^H + x_f x_s^H
+                    po = f2add(f2add(efso, jfeo), cdot2(Ef[l], eso));
                     dPd[l] = pd;
                     dPo[l] = po;
                 }
@@ -276,34 +298,33 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
             }
         }
         // Station terms, row rr (J' = J + x in the trial pass; Hessian: +, trial: -):
-        //   first:  (X J'_s)[rr][.]   = X[rr][rr] J'_s[rr][.] + X[rr][1-rr] J'_s[1-rr][.]
-        //   second: (X^H J'_f)[rr][.] = conj(X[rr][rr]) J'_f[rr][.] + conj(X[1-rr][rr]) J'_f[1-rr][.]
-        // X[1-rr][rr] is the partner lane's Xo.
+        //   first (g, registers): (X J'_s)[rr][.] = X[rr][rr] J'_s[rr][.] + X[rr][1-rr] J'_s[1-rr][.]
+        //   second (shared):      (X^H J'_f)[rr][.] = conj(X[rr][rr]) J'_f[rr][.] + conj(X[1-rr][rr]) J'_f[1-rr][.]
+        // X[1-rr][rr] is the partner lane's Xo; J'_f[rr] is in registers, J'_f[1-rr] in shared memory.
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
             if (k >= K) continue;
             const float2 xp = shfl2x(Xo[k]);
             if (!active) continue;
             float4 sd = Js[(k * N + second) * 2 + rr], so = Js[(k * N + second) * 2 + ro];
-            float4 fd = Js[(k * N + first) * 2 + rr], fo = Js[(k * N + first) * 2 + ro];
+            float4 fd = Jf[k], fo = Js[(k * N + g) * 2 + ro];
             if (!HV) {
                 sd = f4add(sd, Es[(k * N + second) * 2 + rr]);
                 so = f4add(so, Es[(k * N + second) * 2 + ro]);
-                fd = f4add(fd, Es[(k * N + first) * 2 + rr]);
-                fo = f4add(fo, Es[(k * N + first) * 2 + ro]);
+                fd = f4add(fd, Ef[k]);
+                fo = f4add(fo, Es[(k * N + g) * 2 + ro]);
             }
             const float2 v0 = f2add(cmul(Xd[k], make_float2(sd.x, sd.y)), cmul(Xo[k], make_float2(so.x, so.y)));
             const float2 v1 = f2add(cmul(Xd[k], make_float2(sd.z, sd.w)), cmul(Xo[k], make_float2(so.z, so.w)));
             const float2 w0 = f2add(cmul_ca(Xd[k], make_float2(fd.x, fd.y)), cmul_ca(xp, make_float2(fo.x, fo.y)));
             const float2 w1 = f2add(cmul_ca(Xd[k], make_float2(fd.z, fd.w)), cmul_ca(xp, make_float2(fo.z, fo.w)));
-            float4* d1 = acc + (k * N + first) * 2 + rr;
             float4* d2 = accs + (k * N + second) * 2 + rr;
-            const float4 t1 = *d1, t2 = *d2;
+            const float4 t2 = *d2;
             if (HV) {
-                *d1 = make_float4(t1.x + v0.x, t1.y + v0.y, t1.z + v1.x, t1.w + v1.y);
+                A1[k] = make_float4(A1[k].x + v0.x, A1[k].y + v0.y, A1[k].z + v1.x, A1[k].w + v1.y);
                 *d2 = make_float4(t2.x + w0.x, t2.y + w0.y, t2.z + w1.x, t2.w + w1.y);
             } else {
-                *d1 = make_float4(t1.x - v0.x, t1.y - v0.y, t1.z - v1.x, t1.w - v1.y);
+                A1[k] = make_float4(A1[k].x - v0.x, A1[k].y - v0.y, A1[k].z - v1.x, A1[k].w - v1.y);
                 *d2 = make_float4(t2.x - w0.x, t2.y - w0.y, t2.z - w1.x, t2.w - w1.y);
             }
         }
@@ -316,9 +337,12 @@ __global__ void __launch_bounds__(256, 2) k_ss_sweep(const SSArgs a, const int s
 
 template <int KB, bool HV>
 cudaError_t prep_kb() {
-    cudaError_t e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_ss_sweep<KB, HV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, true, false>, attr, 200 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, false, false>, attr, 200 * 1024);
+    if (e == cudaSuccess && !HV) e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, true, !HV>, attr, 200 * 1024);
+    if (e == cudaSuccess && !HV) e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, false, !HV>, attr, 200 * 1024);
+    return e;
 }
 
 template <bool HV>
@@ -338,10 +362,15 @@ cudaError_t prep_all() {
 
 template <int KB, bool HV>
 cudaError_t go(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
-    if (a.K == KB)
-        k_ss_sweep<KB, HV, true><<<grid, threads, smem, s>>>(a, sb);
+    const bool exact = a.K == KB, small = !HV && threads <= 128;  // SMALL only matters for the trial pass
+    if (exact && small)
+        k_ss_sweep<KB, HV, true, !HV><<<grid, threads, smem, s>>>(a, sb);
+    else if (exact)
+        k_ss_sweep<KB, HV, true, false><<<grid, threads, smem, s>>>(a, sb);
+    else if (small)
+        k_ss_sweep<KB, HV, false, !HV><<<grid, threads, smem, s>>>(a, sb);
     else
-        k_ss_sweep<KB, HV, false><<<grid, threads, smem, s>>>(a, sb);
+        k_ss_sweep<KB, HV, false, false><<<grid, threads, smem, s>>>(a, sb);
     return cudaGetLastError();
 }
 
@@ -367,21 +396,21 @@ cudaError_t prepare_ss_kernels() {
     return e != cudaSuccess ? e : prep_all<true>();
 }
 
-size_t ss_sweep_smem_bytes(int N, int K, int slots_max, bool hessvec, int* stage_bytes) {
-    const int KK = K * (K + 1) / 2;
-    const int per_slot = (hessvec ? 0 : K * 32) + KK * 8 + 4;
-    const int sb = ((slots_max * per_slot + 127) / 128) * 128;
+size_t ss_sweep_smem_bytes(int N, int K, bool hessvec, int* stage_bytes) {
+    const int KK = K * (K + 1) / 2, NP = (N + 3) / 4 * 4;
+    const int per_slot = (hessvec ? 0 : K * 32) + KK * 8;
+    const int sb = ((NP * per_slot + 127) / 128) * 128;
     if (stage_bytes) *stage_bytes = sb;
-    return (size_t)NST * sb + BAR_BYTES + (size_t)4 * K * N * 32 + 32 * 8;
+    return (size_t)NST * sb + BAR_BYTES + (size_t)3 * K * N * 32 + 32 * 8;
 }
 
-int ss_sweep_threads(int slots_max) { return ((2 * slots_max + 31) / 32) * 32; }
+int ss_sweep_threads(int N) { return ((2 * ((N + 3) / 4 * 4) + 31) / 32) * 32; }
 
 cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, int grid, cudaStream_t s) {
     int sb = 0;
-    const size_t smem = ss_sweep_smem_bytes(a.N, a.K, a.slots_max, hessvec, &sb);
+    const size_t smem = ss_sweep_smem_bytes(a.N, a.K, hessvec, &sb);
     if (smem > 200 * 1024 || grid < 1 || (long long)grid > (long long)a.A * a.D) return cudaErrorInvalidConfiguration;
-    const int threads = ss_sweep_threads(a.slots_max);
+    const int threads = ss_sweep_threads(a.N);
     return hessvec ? dispatch<true>(a, grid, threads, smem, sb, s) : dispatch<false>(a, grid, threads, smem, sb, s);
 }
 
