@@ -460,8 +460,9 @@ struct Enq {
             pp.kind = ss ? (mode == SWEEP_HESSVEC ? 2 : 3) : (mode == SWEEP_HESSVEC ? 1 : 0);
             cudaEventRecordWithFlags(pp.a, c->stream, cudaEventRecordExternal);
         }
-        if (ss) {
-            ok(launch_ss_sweep(ss_args(c, J, eta), mode == SWEEP_HESSVEC, c->grid_ss, c->stream));
+        if (ss) {  // the statistics trial pass takes the trial point J' itself (written by the last PCG step)
+            const float* e2 = mode == SWEEP_HESSVEC ? eta : c->Jt;
+            ok(launch_ss_sweep(ss_args(c, J, e2), mode == SWEEP_HESSVEC, c->grid_ss, c->stream));
         } else {
             ok(launch_sweep(sweep_args(c, mode, J, eta), mode, c->stream));
         }
@@ -585,7 +586,7 @@ int autotune(calib_ctx* c) {
             }
             if (err != cudaSuccess) return err;
             if (c->formulation == 0)
-                err = launch_ss_sweep(ss_args(c, c->J, c->x), false, c->grid_ss, c->stream);
+                err = launch_ss_sweep(ss_args(c, c->J, c->J), false, c->grid_ss, c->stream);  // J' = J
             else
                 err = launch_sweep(sweep_args(c, SWEEP_TRIAL, c->J, c->x), SWEEP_TRIAL, c->stream);
             if (err != cudaSuccess) return err;

@@ -30,7 +30,9 @@
 namespace calib {
 namespace {
 
-constexpr int NST = 2;   // one stage = one whole diagonal; one stage of prefetch hides the bulk-copy latency
+// One stage = one whole diagonal. Ring depth: the Hessian pass (small stages, 4 CTAs per SM) keeps
+// two stages in flight; the trial pass (larger stages, shared memory for 3 CTAs per SM) one.
+template <bool HV> __host__ __device__ constexpr int nst() { return HV ? 3 : 2; }
 constexpr int BAR_BYTES = 64;  // barrier area, keeps what follows 16-byte aligned
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -62,28 +64,58 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > WAIT_BUDGET_CYCLES) return false;
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 31u) == 0 && clock64() - t0 > WAIT_BUDGET_CYCLES) return false;
     }
-    return true;
 }
 
-__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ float2 cmul_cb(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y); }
-__device__ __forceinline__ float2 cmul_ca(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
 // acc += s * q
 __device__ __forceinline__ void cmac(float2& acc, float2 s, float2 q) {
     acc.x = fmaf(s.x, q.x, fmaf(-s.y, q.y, acc.x));
     acc.y = fmaf(s.x, q.y, fmaf(s.y, q.x, acc.y));
 }
-// a[0] conj(b[0]) + a[1] conj(b[1]) for two complex pairs packed as (re, im, re, im)
-__device__ __forceinline__ float2 cdot2(float4 a, float4 b) {
-    return make_float2(a.x * b.x + a.y * b.y + (a.z * b.z + a.w * b.w), a.y * b.x - a.x * b.y + (a.w * b.z - a.z * b.w));
+// acc + a[0] conj(b[0]) + a[1] conj(b[1]) for complex pairs packed as (re, im, re, im), one FMA chain
+// per component (a conj(b) = (a.x b.x + a.y b.y, a.y b.x - a.x b.y)).
+__device__ __forceinline__ float2 cdot2_acc(float2 acc, float4 a, float4 b) {
+    float re = fmaf(a.x, b.x, acc.x);
+    re = fmaf(a.y, b.y, re);
+    re = fmaf(a.z, b.z, re);
+    re = fmaf(a.w, b.w, re);
+    float im = fmaf(a.y, b.x, acc.y);
+    im = fmaf(-a.x, b.y, im);
+    im = fmaf(a.w, b.z, im);
+    im = fmaf(-a.z, b.w, im);
+    return make_float2(re, im);
 }
-__device__ __forceinline__ float4 f4add(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+// acc + sg (x0 b0 + x1 b1) (complex products; sg = +1 or -1 folded into the FMAs).
+__device__ __forceinline__ float2 cmul2_acc(float2 acc, float sg, float2 x0, float2 b0, float2 x1, float2 b1) {
+    float re = fmaf(sg * x0.x, b0.x, acc.x);
+    re = fmaf(-sg * x0.y, b0.y, re);
+    re = fmaf(sg * x1.x, b1.x, re);
+    re = fmaf(-sg * x1.y, b1.y, re);
+    float im = fmaf(sg * x0.x, b0.y, acc.y);
+    im = fmaf(sg * x0.y, b0.x, im);
+    im = fmaf(sg * x1.x, b1.y, im);
+    im = fmaf(sg * x1.y, b1.x, im);
+    return make_float2(re, im);
+}
+// acc + sg (conj(x0) b0 + conj(x1) b1); conj(x) b = (x.x b.x + x.y b.y, x.x b.y - x.y b.x).
+__device__ __forceinline__ float2 cmul2c_acc(float2 acc, float sg, float2 x0, float2 b0, float2 x1, float2 b1) {
+    float re = fmaf(sg * x0.x, b0.x, acc.x);
+    re = fmaf(sg * x0.y, b0.y, re);
+    re = fmaf(sg * x1.x, b1.x, re);
+    re = fmaf(sg * x1.y, b1.y, re);
+    float im = fmaf(sg * x0.x, b0.y, acc.y);
+    im = fmaf(-sg * x0.y, b0.x, im);
+    im = fmaf(sg * x1.x, b1.y, im);
+    im = fmaf(-sg * x1.y, b1.x, im);
+    return make_float2(re, im);
+}
+__device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
 // value of the partner lane (lane ^ 1: the other row of the same slot)
 __device__ __forceinline__ float2 shfl2x(float2 v) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1));
@@ -100,6 +132,8 @@ __device__ __forceinline__ long long cta_of_item(long long i, long long W, long 
 template <int KB, bool HV, bool EXACT, bool SMALL>
 __global__ void __launch_bounds__((!HV && SMALL) ? 128 : 256, HV ? 2 : (SMALL ? 3 : 1))
     k_ss_sweep(const SSArgs a, const int stage_bytes) {
+    constexpr int NST = nst<HV>();
+    constexpr float sg = HV ? 1.f : -1.f;  // station terms: + in the Hessian pass, - (gradient) in the trial pass
     extern __shared__ __align__(128) unsigned char smem[];
     const int N = a.N, D = a.D, NP = a.NP;
     const int K = EXACT ? KB : a.K;
@@ -113,7 +147,7 @@ __global__ void __launch_bounds__((!HV && SMALL) ? 128 : 256, HV ? 2 : (SMALL ? 
     unsigned char* stage = smem;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NST * stage_bytes);
     float4* Js = reinterpret_cast<float4*>(smem + NST * stage_bytes + BAR_BYTES);  // [K][N][2 rows]
-    float4* Es = Js + KN2;     // eta (Hessian) or x (trial)
+    float4* Es = Js + KN2;     // eta (Hessian) or the trial point J' = J + x (trial)
     float4* accs = Es + KN2;   // second-station sums
     double* red = reinterpret_cast<double*>(accs + KN2);  // [32]
 
@@ -143,9 +177,10 @@ __global__ void __launch_bounds__((!HV && SMALL) ? 128 : 256, HV ? 2 : (SMALL ? 
         if (!HV) bulk_g2s(buf, a.U + blk * K * 4, ub, b);
         bulk_g2s(buf + ub, a.S + blk * KK, sb, b);
     };
-    if (tid == 0 && S > 0) issue(0);
+    if (tid == 0)
+        for (int s2 = 0; s2 < min(NST - 1, S); ++s2) issue(s2);
 
-    float4 Jf[KB], Ef[KB], A1[KB];  // rows rr of station g's J and eta / x; its first-station sums
+    float4 Jf[KB], Ef[KB], A1[KB];  // rows rr of station g's J and eta / J'; its first-station sums
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
     for (int k = 0; k < KB; ++k) Jf[k] = Ef[k] = A1[k] = z4;
@@ -210,9 +245,9 @@ __global__ void __launch_bounds__((!HV && SMALL) ? 128 : 256, HV ? 2 : (SMALL ? 
             }
             return;
         }
-        if (tid == 0 && s + 1 < S) {
+        if (tid == 0 && s + NST - 1 < S) {
             fence_proxy_async_smem();
-            issue(s + 1);
+            issue(s + NST - 1);
         }
         if (fresh) {  // station g's rows of the new agent
             fresh = false;
@@ -247,21 +282,21 @@ __global__ void __launch_bounds__((!HV && SMALL) ? 128 : 256, HV ? 2 : (SMALL ? 
 #pragma unroll
             for (int l = 0; l < KB; ++l) {
                 if (l >= K) continue;
-                // rows rr and 1 - rr of the second station's blocks
+                // rows rr and 1 - rr of the second station's blocks; (A B^H)[rr][c] = A[rr][0] conj(B[c][0]) +
+                // A[rr][1] conj(B[c][1]) for the columns c = rr (d) and 1 - rr (o)
                 const float4 jsd = Js[(l * N + second) * 2 + rr], jso = Js[(l * N + second) * 2 + ro];
                 const float4 esd = Es[(l * N + second) * 2 + rr], eso = Es[(l * N + second) * 2 + ro];
-                // (A B^H)[rr][c] = A[rr][0] conj(B[c][0]) + A[rr][1] conj(B[c][1]), c = rr (d) and 1 - rr (o)
-                const float2 efsd = cdot2(Ef[l], jsd), efso = cdot2(Ef[l], jso);
-                const float2 jfed = cdot2(Jf[l], esd), jfeo = cdot2(Jf[l], eso);
-                float2 qd, qo, pd = make_float2(0.f, 0.f), po = make_float2(0.f, 0.f);
-                if (HV) {
-                    qd = f2add(efsd, jfed);  // Q_l = eta_f J_s^H + J_f eta_s^H
-                    qo = f2add(efso, jfeo);
-                } else {
-                    qd = cdot2(Jf[l], jsd);  // P_l = J_f J_s^H
-                    qo = cdot2(Jf[l], jso);
-                    pd = f2add(f2add(efsd, jfed), cdot2(Ef[l], esd));  // dP_l = x_f J_s^H + J_f x_s^H + x_f x_s^H
-                    po = f2add(f2add(efso, jfeo), cdot2(Ef[l], eso));
+                const float2 z2 = make_float2(0.f, 0.f);
+                float2 qd, qo, pd = z2, po = z2;
+                if (HV) {  // Q_l = eta_f J_s^H + J_f eta_s^H
+                    qd = cdot2_acc(cdot2_acc(z2, Ef[l], jsd), Jf[l], esd);
+                    qo = cdot2_acc(cdot2_acc(z2, Ef[l], jso), Jf[l], eso);
+                } else {   // P_l = J_f J_s^H;  dP_l = J'_f J'_s^H - P_l = x_f J'_s^H + J_f x_s^H, x = J' - J
+                    const float4 xf = f4sub(Ef[l], Jf[l]);
+                    qd = cdot2_acc(z2, Jf[l], jsd);
+                    qo = cdot2_acc(z2, Jf[l], jso);
+                    pd = cdot2_acc(cdot2_acc(z2, xf, esd), Jf[l], f4sub(esd, jsd));
+                    po = cdot2_acc(cdot2_acc(z2, xf, eso), Jf[l], f4sub(eso, jso));
                     dPd[l] = pd;
                     dPo[l] = po;
                 }
@@ -301,32 +336,22 @@ __global__ void __launch_bounds__((!HV && SMALL) ? 128 : 256, HV ? 2 : (SMALL ? 
         //   first (g, registers): (X J'_s)[rr][.] = X[rr][rr] J'_s[rr][.] + X[rr][1-rr] J'_s[1-rr][.]
         //   second (shared):      (X^H J'_f)[rr][.] = conj(X[rr][rr]) J'_f[rr][.] + conj(X[1-rr][rr]) J'_f[1-rr][.]
         // X[1-rr][rr] is the partner lane's Xo; J'_f[rr] is in registers, J'_f[1-rr] in shared memory.
+        const float4* Jp = HV ? Js : Es;  // J' (the Hessian pass is taken at J)
 #pragma unroll
         for (int k = 0; k < KB; ++k) {
             if (k >= K) continue;
             const float2 xp = shfl2x(Xo[k]);
             if (!active) continue;
-            float4 sd = Js[(k * N + second) * 2 + rr], so = Js[(k * N + second) * 2 + ro];
-            float4 fd = Jf[k], fo = Js[(k * N + g) * 2 + ro];
-            if (!HV) {
-                sd = f4add(sd, Es[(k * N + second) * 2 + rr]);
-                so = f4add(so, Es[(k * N + second) * 2 + ro]);
-                fd = f4add(fd, Ef[k]);
-                fo = f4add(fo, Es[(k * N + g) * 2 + ro]);
-            }
-            const float2 v0 = f2add(cmul(Xd[k], make_float2(sd.x, sd.y)), cmul(Xo[k], make_float2(so.x, so.y)));
-            const float2 v1 = f2add(cmul(Xd[k], make_float2(sd.z, sd.w)), cmul(Xo[k], make_float2(so.z, so.w)));
-            const float2 w0 = f2add(cmul_ca(Xd[k], make_float2(fd.x, fd.y)), cmul_ca(xp, make_float2(fo.x, fo.y)));
-            const float2 w1 = f2add(cmul_ca(Xd[k], make_float2(fd.z, fd.w)), cmul_ca(xp, make_float2(fo.z, fo.w)));
+            const float4 sd = Jp[(k * N + second) * 2 + rr], so = Jp[(k * N + second) * 2 + ro];
+            const float4 fd = HV ? Jf[k] : Ef[k], fo = Jp[(k * N + g) * 2 + ro];
+            const float2 a0 = cmul2_acc(make_float2(A1[k].x, A1[k].y), sg, Xd[k], make_float2(sd.x, sd.y), Xo[k], make_float2(so.x, so.y));
+            const float2 a1 = cmul2_acc(make_float2(A1[k].z, A1[k].w), sg, Xd[k], make_float2(sd.z, sd.w), Xo[k], make_float2(so.z, so.w));
+            A1[k] = make_float4(a0.x, a0.y, a1.x, a1.y);
             float4* d2 = accs + (k * N + second) * 2 + rr;
             const float4 t2 = *d2;
-            if (HV) {
-                A1[k] = make_float4(A1[k].x + v0.x, A1[k].y + v0.y, A1[k].z + v1.x, A1[k].w + v1.y);
-                *d2 = make_float4(t2.x + w0.x, t2.y + w0.y, t2.z + w1.x, t2.w + w1.y);
-            } else {
-                A1[k] = make_float4(A1[k].x - v0.x, A1[k].y - v0.y, A1[k].z - v1.x, A1[k].w - v1.y);
-                *d2 = make_float4(t2.x - w0.x, t2.y - w0.y, t2.z - w1.x, t2.w - w1.y);
-            }
+            const float2 b0 = cmul2c_acc(make_float2(t2.x, t2.y), sg, Xd[k], make_float2(fd.x, fd.y), xp, make_float2(fo.x, fo.y));
+            const float2 b1 = cmul2c_acc(make_float2(t2.z, t2.w), sg, Xd[k], make_float2(fd.z, fd.w), xp, make_float2(fo.z, fo.w));
+            *d2 = make_float4(b0.x, b0.y, b1.x, b1.y);
         }
     }
     if (agent >= 0) {
@@ -401,7 +426,8 @@ size_t ss_sweep_smem_bytes(int N, int K, bool hessvec, int* stage_bytes) {
     const int per_slot = (hessvec ? 0 : K * 32) + KK * 8;
     const int sb = ((NP * per_slot + 127) / 128) * 128;
     if (stage_bytes) *stage_bytes = sb;
-    return (size_t)NST * sb + BAR_BYTES + (size_t)3 * K * N * 32 + 32 * 8;
+    const int nstages = hessvec ? nst<true>() : nst<false>();
+    return (size_t)nstages * sb + BAR_BYTES + (size_t)3 * K * N * 32 + 32 * 8;
 }
 
 int ss_sweep_threads(int N) { return ((2 * ((N + 3) / 4 * 4) + 31) / 32) * 32; }

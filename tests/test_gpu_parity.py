@@ -171,11 +171,14 @@ def test_admm_history_matches_oracle(lib, case, form):
 @pytest.mark.parametrize("case,n_cg", [("n3_k2", 1), ("tiny_n8_k1", 4), ("ragged_n13_k3", 4)])
 def test_admm_one_lm_step_matches_all_records(lib, case, n_cg, form):
     """n_lm = 1 (and n_cg = 1: one preconditioned steepest-descent step): the gauge mode is
-    not resolved, so primal and dual residuals agree at 1e-4 as well."""
+    not resolved, so primal and dual residuals agree at 1e-4 as well. The dual residual is the
+    norm of a difference of consecutive Z (Section 4): its float32 round-off is absolute, of the
+    order of Z's own, so it gets the floor 1e-5 x its first record (as in the full history test)."""
     prob = CASES[case]()
     _, hist, ref = run_both(lib, prob, 3, n_lm=1, n_cg=n_cg, form=form)
     for key in ("objective", "resid_norm", "primal", "dual"):
-        np.testing.assert_allclose(hist[key], ref[key], rtol=REL_ADMM, atol=1e-9, err_msg=key)
+        atol = 1e-5 * ref[key][0] if key == "dual" else 1e-9
+        np.testing.assert_allclose(hist[key], ref[key], rtol=REL_ADMM, atol=atol, err_msg=key)
 
 
 def test_admm_solutions_match_oracle_after_gauge(lib):
