@@ -227,9 +227,10 @@ def run_ours(args, world, rank, local):
 
     # the sweep split the autotuner picks for this shape (what the first calib_admm_iter would do)
     capi.calib_predict(cal.ctx, uvw_d, sky_d, prob["f0"])
-    split, split_ms = (args.ctas_per_sm if args.formulation == "statistics" else args.chunk_diagonals), None
+    split = args.ctas_per_sm if args.formulation == "statistics" else args.chunk_diagonals
+    split_tr, split_ms = split, None
     if split == 0:
-        split, split_ms = capi.calib_autotune(cal.ctx)
+        split, split_tr, split_ms = capi.calib_autotune(cal.ctx)
 
     def barrier():
         if world > 1:
@@ -338,8 +339,8 @@ def run_ours(args, world, rank, local):
                        "subbands": prob["P"], "intervals": prob["I"], "samples": 10, "admm_iters": n_admm,
                        "n_lm": N_LM, "n_cg": N_CG, "basis": "Bernstein degree 3", "rho": 10.0,
                        "formulation": args.formulation,
-                       ("ctas_per_sm" if args.formulation == "statistics" else "chunk_diagonals"): split,
-                       "autotune_ms_per_lm_step": split_ms,
+                       ("ctas_per_sm" if args.formulation == "statistics" else "chunk_diagonals"): [split, split_tr],
+                       "autotune_ms_hessian_trial": split_ms,
                        "step": "predict + cold start + 30 C-ADMM iterations",
                        "l2": "inputs larger than L2 (436 MB per residual sweep, 242 MB per Hessian sweep)",
                        "parallelism": f"replica x{world}" if world > 1 else "single GPU",

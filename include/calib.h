@@ -181,16 +181,17 @@ int calib_profile_enable(calib_ctx* ctx, int on);
 int calib_profile_read(calib_ctx* ctx, int cap, const char** names, double* total_ms,
                        long long* launches, double* bytes_per_launch, double* flops_per_launch);
 
-/* Autotuner: time one LM step (n_cg Hessian passes with their PCG steps, one trial pass and its
- * reduction) on the loaded data for each candidate work split and keep the fastest. The split is
- * CTAs per SM (1, 2, 3, 4, 6, 8, 12, 16, 24) for CALIB_FORM_STATISTICS and diagonals per CTA
- * (1, 2, 4, ..., N/2) for CALIB_FORM_DIRECT. calib_admm_iter runs it by itself before its first
- * iteration when the option that fixes the split (ctas_per_sm or chunk_diagonals) is 0; the
- * choice is cached per problem shape for the process. This call re-measures. Outputs (host, any
- * may be NULL): the chosen split, up to cap candidates and their milliseconds per LM step, and the
- * candidate count. The iteration state (J, Z, Y) is not changed. */
-int calib_autotune(calib_ctx* ctx, int* split, int cap, int* candidates,
-                   double* ms_per_lm_step, int* n_candidates);
+/* Autotuner: time the two halves of one LM step on the loaded data - n_cg Hessian passes with
+ * their PCG steps, and the trial pass with its reduction - for each candidate work split. The
+ * split is CTAs per SM (1, 2, 3, 4, 6, 8, 12, 16, 24) for CALIB_FORM_STATISTICS, chosen per pass,
+ * and diagonals per CTA (1, 2, 4, ..., N/2) for CALIB_FORM_DIRECT, one value for both passes (the
+ * fastest whole step). calib_admm_iter runs it by itself before its first iteration when the
+ * option that fixes the split (ctas_per_sm or chunk_diagonals) is 0; the choice is cached per
+ * problem shape for the process. This call re-measures. Outputs (host, any may be NULL): the
+ * chosen split of the Hessian and of the trial pass, up to cap candidates with the milliseconds of
+ * each half, and the candidate count. The iteration state (J, Z, Y) is not changed. */
+int calib_autotune(calib_ctx* ctx, int* split, int* split_trial, int cap, int* candidates,
+                   double* ms_hessian, double* ms_trial, int* n_candidates);
 
 /* ---- Learned warm start (the paper starts a calibration from the previous time slot's solution,
  * Section 3, initialisation; a small network refines that start).

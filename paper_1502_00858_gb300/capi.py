@@ -79,7 +79,7 @@ def load(path: str = LIB_PATH):
         "calib_last_error": (C.c_char_p, []),
         "calib_destroy": (None, [vp]),
         "calib_eval_noalloc": (i, [i, i, i, i, i, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]),
-        "calib_autotune": (i, [vp, vp, i, vp, vp, vp]),
+        "calib_autotune": (i, [vp, vp, vp, i, vp, vp, vp, vp]),
         "calib_mlp_create": (i, [C.POINTER(vp), i, i, i, i, vp]),
         "calib_mlp_num_params": (C.c_longlong, [vp]),
         "calib_mlp_set_weights": (i, [vp, vp, i]),
@@ -274,15 +274,17 @@ def calib_eval_noalloc(n_agents, n_stations, n_baselines, n_dirs, n_samples, pq,
 
 
 def calib_autotune(ctx):
-    """Re-measure the sweep split; returns (chosen split, {candidate: ms per LM step}). The split is
-    CTAs per SM (statistics form) or diagonals per CTA (direct form)."""
+    """Re-measure the sweep split. Returns (split of the Hessian pass, split of the trial pass,
+    {candidate: (ms of n_cg Hessian passes with PCG steps, ms of the trial pass with its reduction)}).
+    The split is CTAs per SM (statistics form) or diagonals per CTA (direct form, one value)."""
     cap = 64
-    chosen = C.c_int()
+    chosen, chosen_tr = C.c_int(), C.c_int()
     cand = np.zeros(cap, dtype=np.int32)
-    ms = np.zeros(cap)
+    ms_hv, ms_tr = np.zeros(cap), np.zeros(cap)
     n = C.c_int()
-    _check(load().calib_autotune(ctx, C.byref(chosen), cap, cand.ctypes.data, ms.ctypes.data, C.byref(n)))
-    return chosen.value, {int(cand[i]): float(ms[i]) for i in range(n.value)}
+    _check(load().calib_autotune(ctx, C.byref(chosen), C.byref(chosen_tr), cap, cand.ctypes.data, ms_hv.ctypes.data,
+                                 ms_tr.ctypes.data, C.byref(n)))
+    return chosen.value, chosen_tr.value, {int(cand[i]): (float(ms_hv[i]), float(ms_tr[i])) for i in range(n.value)}
 
 
 # ----------------------------------------------------------------------------- warm-start network

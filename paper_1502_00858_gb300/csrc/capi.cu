@@ -50,15 +50,24 @@ struct GraphEntry {
 
 }  // namespace
 
+struct TuneEntry {
+    int v;          // candidate split
+    double hv, tr;  // ms: n_cg Hessian passes with their PCG steps; the trial pass with its reduction
+};
+
 struct calib_ctx {
     int dev = 0;
     int N = 0, B = 0, K = 0, P = 0, M = 0, I = 0, A = 0, D = 0;
     int n_lm = 10, n_cg = 4, chunk_diags = 1, n_chunks = 1, slots_max = 4;
     bool tune_pending = false;     // work split chosen by the autotuner at the first iteration
-    // statistics sweeps: grid = sms * ctas_per_sm CTAs (at most A*D), balanced contiguous item ranges
-    int sms = 1, ctas_per_sm = 4, grid_ss = 1, stride_ss = 1;
-    int* pn_ss = nullptr;          // [A] pieces (CTAs) meeting each agent
-    std::vector<std::pair<int, double>> tune_log;  // (diagonals per CTA, ms per LM step)
+    // statistics sweeps: grid = sms * m CTAs (at most A*D), balanced contiguous item ranges; the
+    // Hessian and trial passes are split independently
+    int sms = 1;
+    struct Partition {
+        int m = 4, grid = 1, stride = 1;
+        int* pn = nullptr;         // [A] pieces (CTAs) meeting each agent
+    } part_hv, part_tr;
+    std::vector<TuneEntry> tune_log;  // per candidate split: ms of the Hessian half and of the trial half
     int TT_res = 1, TT_hv = 1;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -150,13 +159,18 @@ SweepArgs sweep_args(calib_ctx* c, int mode, const float* J, const float* eta) {
 
 // ss_parts: the partials come from a statistics sweep (per-agent piece counts), else from a
 // direct sweep (n_chunks per agent).
-LMArgs lm_args(calib_ctx* c, bool ss_parts) {
+enum PartsFrom { PARTS_DIRECT, PARTS_SS_HESSIAN, PARTS_SS_TRIAL };
+
+// Where the partials the LM kernel reduces come from: a direct sweep (n_chunks per agent) or a
+// statistics sweep (per-agent piece counts of its partition).
+LMArgs lm_args(calib_ctx* c, PartsFrom from) {
     LMArgs a{};
     a.part = c->part;
     a.part_cost = c->part_cost;
     a.part_dcost = c->part_dcost;
-    a.part_n = ss_parts ? c->pn_ss : nullptr;
-    a.part_stride = ss_parts ? c->stride_ss : c->n_chunks;
+    const calib_ctx::Partition* pt = from == PARTS_SS_HESSIAN ? &c->part_hv : from == PARTS_SS_TRIAL ? &c->part_tr : nullptr;
+    a.part_n = pt ? pt->pn : nullptr;
+    a.part_stride = pt ? pt->stride : c->n_chunks;
     a.J = c->J;
     a.Jt = c->Jt;
     a.Y = c->Y;
@@ -179,7 +193,7 @@ LMArgs lm_args(calib_ctx* c, bool ss_parts) {
     return a;
 }
 
-SSArgs ss_args(calib_ctx* c, const float* J, const float* eta) {
+SSArgs ss_args(calib_ctx* c, const float* J, const float* eta, bool hessvec) {
     SSArgs a{};
     a.U = c->ssU;
     a.S = c->ssS;
@@ -193,14 +207,14 @@ SSArgs ss_args(calib_ctx* c, const float* J, const float* eta) {
     a.K = c->K;
     a.D = c->D;
     a.NP = (c->N + 3) / 4 * 4;
-    a.part_stride = c->stride_ss;
+    a.part_stride = hessvec ? c->part_hv.stride : c->part_tr.stride;
     return a;
 }
 
 // Split the A*D items of the statistics sweeps over grid = min(A*D, sms * m) CTAs and record how
 // many CTAs meet each agent (the pieces its reductions sum). CTA c takes items
 // [floor(c W / G), floor((c+1) W / G)); item i lies in CTA ((i+1) G - 1) / W.
-int set_partition(calib_ctx* c, int m) {
+int set_partition(calib_ctx* c, calib_ctx::Partition& pt, int m) {
     const long long W = (long long)c->A * c->D;
     const long long G = std::max(1LL, std::min(W, (long long)c->sms * m));
     std::vector<int> pn(c->A);
@@ -211,10 +225,10 @@ int set_partition(calib_ctx* c, int m) {
         pn[a] = (int)(c1 - c0 + 1);
         stride = std::max(stride, pn[a]);
     }
-    CK(cudaMemcpy(c->pn_ss, pn.data(), pn.size() * sizeof(int), cudaMemcpyHostToDevice));
-    c->ctas_per_sm = m;
-    c->grid_ss = (int)G;
-    c->stride_ss = stride;
+    CK(cudaMemcpy(pt.pn, pn.data(), pn.size() * sizeof(int), cudaMemcpyHostToDevice));
+    pt.m = m;
+    pt.grid = (int)G;
+    pt.stride = stride;
     return CALIB_OK;
 }
 
@@ -462,7 +476,8 @@ struct Enq {
         }
         if (ss) {  // the statistics trial pass takes the trial point J' itself (written by the last PCG step)
             const float* e2 = mode == SWEEP_HESSVEC ? eta : c->Jt;
-            ok(launch_ss_sweep(ss_args(c, J, e2), mode == SWEEP_HESSVEC, c->grid_ss, c->stream));
+            const bool hv = mode == SWEEP_HESSVEC;
+            ok(launch_ss_sweep(ss_args(c, J, e2, hv), hv, hv ? c->part_hv.grid : c->part_tr.grid, c->stream));
         } else {
             ok(launch_sweep(sweep_args(c, mode, J, eta), mode, c->stream));
         }
@@ -475,18 +490,20 @@ struct Enq {
 
 void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
     calib_ctx* c = q.c;
-    const LMArgs la = lm_args(c, c->formulation == 0);  // after the iteration's own sweeps
+    const bool ssf = c->formulation == 0;
+    const LMArgs la_hv = lm_args(c, ssf ? PARTS_SS_HESSIAN : PARTS_DIRECT);  // after a Hessian sweep
+    const LMArgs la = lm_args(c, ssf ? PARTS_SS_TRIAL : PARTS_DIRECT);       // after the trial sweep
     const ConsArgs ca = cons_args(c);
     if (eval_first) {  // the residual sweep is the direct one in both formulations (it yields g exactly)
         q.sweep(SWEEP_RESIDUAL, c->J, nullptr);
-        q.ok(launch_lm_eval(lm_args(c, false), LM_BEGIN_FROM_PARTIALS, c->stream));
+        q.ok(launch_lm_eval(lm_args(c, PARTS_DIRECT), LM_BEGIN_FROM_PARTIALS, c->stream));
     } else {
         q.ok(launch_lm_eval(la, LM_BEGIN_REUSE, c->stream));
     }
     for (int l = 0; l < c->n_lm; ++l) {
         for (int k = 0; k < c->n_cg; ++k) {
             q.sweep(SWEEP_HESSVEC, c->J, c->p);
-            q.ok(launch_cg_step(la, k == c->n_cg - 1, c->stream));  // the last one forms the trial point
+            q.ok(launch_cg_step(la_hv, k == c->n_cg - 1, c->stream));  // the last one forms the trial point
         }
         q.sweep(SWEEP_TRIAL, c->J, c->x);
         q.ok(launch_lm_eval(la, LM_ACCEPT, c->stream));
@@ -518,20 +535,25 @@ struct TuneKey {
         return std::tie(N, K, A, D, form, n_cg, work) < std::tie(o.N, o.K, o.A, o.D, o.form, o.n_cg, o.work);
     }
 };
-std::map<TuneKey, int>& tune_cache() {
-    static std::map<TuneKey, int> m;
+struct TuneResult { int hv, tr; };  // split of the Hessian and of the trial pass
+std::map<TuneKey, TuneResult>& tune_cache() {
+    static std::map<TuneKey, TuneResult> m;
     return m;
 }
 
-// Time one LM step (n_cg Hessian passes and PCG steps, one trial pass and its reduction) for each
-// candidate work split and keep the fastest: CTAs per SM of the statistics sweeps, or diagonals per
-// CTA of the direct sweeps. Runs on the context's data; touches only scratch outputs and the PCG
+// Time the two halves of one LM step - n_cg Hessian passes with their PCG steps, and the trial
+// pass with its reduction - for each candidate work split and keep the fastest: CTAs per SM of
+// each statistics sweep (chosen per pass), or diagonals per CTA of the direct sweeps (one value,
+// the fastest whole step). Runs on the context's data; touches only scratch outputs and the PCG
 // vectors x, r, p, which the next LM begin re-initialises (the PCG steps run in timing mode and
 // write no agent state).
-int apply_split(calib_ctx* c, int v) {
-    if (c->formulation == 0) return set_partition(c, v);
-    c->chunk_diags = v;
-    c->n_chunks = (c->D + v - 1) / v;
+int apply_split(calib_ctx* c, TuneResult v) {
+    if (c->formulation == 0) {
+        const int rc = set_partition(c, c->part_hv, v.hv);
+        return rc ? rc : set_partition(c, c->part_tr, v.tr);
+    }
+    c->chunk_diags = v.hv;
+    c->n_chunks = (c->D + v.hv - 1) / v.hv;
     return CALIB_OK;
 }
 
@@ -563,56 +585,68 @@ int autotune(calib_ctx* c) {
         for (int cd = 1; cd <= c->D; cd *= 2) cands.push_back(cd);
         if (cands.back() != c->D) cands.push_back(c->D);
     }
-    cudaEvent_t e0, e1;
+    cudaEvent_t e0, e1, e2;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    double best = 1e300;
-    int best_v = cands.front();
+    CK(cudaEventCreate(&e2));
+    const bool ssf = c->formulation == 0;
+    double best_hv = 1e300, best_tr = 1e300, best_sum = 1e300;
+    TuneResult best{cands.front(), cands.front()};
+    int best_direct = cands.front();
     const int reps = 3;
     for (int v : cands) {
-        const int rc = apply_split(c, v);
+        const int rc = apply_split(c, TuneResult{v, v});
         if (rc) return rc;
-        LMArgs la = lm_args(c, c->formulation == 0);
-        la.Jt = c->J;
-        la.timing = 1;
-        auto one_step = [&]() -> cudaError_t {
+        LMArgs la_hv = lm_args(c, ssf ? PARTS_SS_HESSIAN : PARTS_DIRECT);
+        LMArgs la_tr = lm_args(c, ssf ? PARTS_SS_TRIAL : PARTS_DIRECT);
+        la_hv.timing = 1;
+        la_tr.Jt = c->J;
+        auto hessian_half = [&]() -> cudaError_t {
             cudaError_t err = cudaSuccess;
             for (int k = 0; k < c->n_cg && err == cudaSuccess; ++k) {
-                if (c->formulation == 0)
-                    err = launch_ss_sweep(ss_args(c, c->J, c->p), true, c->grid_ss, c->stream);
+                if (ssf)
+                    err = launch_ss_sweep(ss_args(c, c->J, c->p, true), true, c->part_hv.grid, c->stream);
                 else
                     err = launch_sweep(sweep_args(c, SWEEP_HESSVEC, c->J, c->p), SWEEP_HESSVEC, c->stream);
-                if (err == cudaSuccess) err = launch_cg_step(la, false, c->stream);
+                if (err == cudaSuccess) err = launch_cg_step(la_hv, false, c->stream);
             }
-            if (err != cudaSuccess) return err;
-            if (c->formulation == 0)
-                err = launch_ss_sweep(ss_args(c, c->J, c->J), false, c->grid_ss, c->stream);  // J' = J
+            return err;
+        };
+        auto trial_half = [&]() -> cudaError_t {
+            cudaError_t err;
+            if (ssf)
+                err = launch_ss_sweep(ss_args(c, c->J, c->J, false), false, c->part_tr.grid, c->stream);  // J' = J
             else
                 err = launch_sweep(sweep_args(c, SWEEP_TRIAL, c->J, c->x), SWEEP_TRIAL, c->stream);
-            if (err != cudaSuccess) return err;
-            return launch_eval_output(la, c->evOut, c->evL, c->evG, c->stream);
+            return err != cudaSuccess ? err : launch_eval_output(la_tr, c->evOut, c->evL, c->evG, c->stream);
         };
-        CK(one_step());  // warm
+        CK(hessian_half());  // warm
+        CK(trial_half());
         CK(cudaEventRecord(e0, c->stream));
-        for (int r = 0; r < reps; ++r) CK(one_step());
+        for (int r = 0; r < reps; ++r) CK(hessian_half());
         CK(cudaEventRecord(e1, c->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        const double per = ms / reps;
+        for (int r = 0; r < reps; ++r) CK(trial_half());
+        CK(cudaEventRecord(e2, c->stream));
+        CK(cudaEventSynchronize(e2));
+        float ms_hv = 0.f, ms_tr = 0.f;
+        CK(cudaEventElapsedTime(&ms_hv, e0, e1));
+        CK(cudaEventElapsedTime(&ms_tr, e1, e2));
+        ms_hv /= reps;
+        ms_tr /= reps;
         c->launches += (long long)(reps + 1) * (2 * c->n_cg + 2);
-        c->tune_log.emplace_back(v, per);
-        if (per < best) {
-            best = per;
-            best_v = v;
-        }
+        c->tune_log.push_back(TuneEntry{v, ms_hv, ms_tr});
+        if (ms_hv < best_hv) { best_hv = ms_hv; best.hv = v; }
+        if (ms_tr < best_tr) { best_tr = ms_tr; best.tr = v; }
+        if (ms_hv + ms_tr < best_sum) { best_sum = ms_hv + ms_tr; best_direct = v; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    const int rc = apply_split(c, best_v);
+    cudaEventDestroy(e2);
+    if (!ssf) best = TuneResult{best_direct, best_direct};
+    const int rc = apply_split(c, best);
     if (rc) return rc;
     c->tune_pending = false;
-    tune_cache()[key] = best_v;
+    tune_cache()[key] = best;
     clear_graphs(c);
     return check_status(c);
 }
@@ -713,7 +747,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     }
     c->n_chunks = (c->D + c->chunk_diags - 1) / c->chunk_diags;
     if (opt.ctas_per_sm > 0) {
-        c->ctas_per_sm = opt.ctas_per_sm;
+        c->part_hv.m = c->part_tr.m = opt.ctas_per_sm;
     } else if (c->formulation == 0) {
         c->tune_pending = true;
     }
@@ -751,7 +785,8 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     okm = okm && dalloc(&c->dual2, (size_t)c->I * K) == cudaSuccess;
     okm = okm && dalloc(&c->iter_counter, 1) == cudaSuccess && dalloc(&c->status, 1) == cudaSuccess;
     okm = okm && dalloc(&c->evL, (size_t)A) == cudaSuccess && dalloc(&c->evG, (size_t)A) == cudaSuccess;
-    okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess && dalloc(&c->pn_ss, (size_t)A) == cudaSuccess;
+    okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess && dalloc(&c->part_hv.pn, (size_t)A) == cudaSuccess &&
+          dalloc(&c->part_tr.pn, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->vis_off_d, (size_t)A) == cudaSuccess && dalloc(&c->coh_off_d, (size_t)A) == cudaSuccess;
     if (!okm) return bail(fail(CALIB_ENOMEM, "device allocation failed"));
     if (ensure_stats(c, 64) != CALIB_OK) return bail(CALIB_ENOMEM);
@@ -769,7 +804,8 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
         return bail(fail(CALIB_ECUDA, "cannot read the SM count"));
     int rc = build_layout(c, nullptr);
     if (rc) return bail(rc);
-    rc = set_partition(c, c->ctas_per_sm);
+    rc = set_partition(c, c->part_hv, c->part_hv.m);
+    if (rc == CALIB_OK) rc = set_partition(c, c->part_tr, c->part_tr.m);
     if (rc) return bail(rc);
     rc = calib_reset(c);
     if (rc) return bail(rc);
@@ -1053,7 +1089,7 @@ int calib_eval(calib_ctx* c, const void* Jin, double* L, double* g, void* grad, 
     CK(cudaMemcpyAsync(c->evJ, Jin, vb, ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     CK(launch_sweep(sweep_args(c, SWEEP_RESIDUAL, c->evJ, nullptr), SWEEP_RESIDUAL, c->stream));
-    LMArgs la = lm_args(c, false);  // after a direct sweep
+    LMArgs la = lm_args(c, PARTS_DIRECT);
     la.Jt = c->evJ;
     CK(launch_eval_output(la, c->evOut, c->evL, c->evG, c->stream));
     c->launches += 2;
@@ -1078,7 +1114,7 @@ int calib_hessvec(calib_ctx* c, const void* Jin, const void* eta, void* out, int
     CK(cudaMemcpyAsync(c->evE, eta, vb, kind, c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     CK(launch_sweep(sweep_args(c, SWEEP_HESSVEC, c->evJ, c->evE), SWEEP_HESSVEC, c->stream));
-    LMArgs la = lm_args(c, false);  // after a direct sweep
+    LMArgs la = lm_args(c, PARTS_DIRECT);
     la.p = c->evE;
     CK(launch_hv_output(la, c->evOut, c->stream));
     c->launches += 2;
@@ -1173,7 +1209,7 @@ int calib_warm_start(calib_ctx* c, calib_mlp* mlp, const void* J_prev, const voi
                        ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     if (mlp) {
         CK(mlp_warm_rows(mlp, c->ws_prev, c->BZ, c->xf_d, c->K, c->N, c->A, c->ws_mlp, c->stream));
-        LMArgs la = lm_args(c, false);  // after a direct sweep
+        LMArgs la = lm_args(c, PARTS_DIRECT);
         const float* starts[2] = {c->ws_mlp, c->ws_prev};
         for (int i = 0; i < 2; ++i) {
             CK(launch_sweep(sweep_args(c, SWEEP_RESIDUAL, starts[i], nullptr), SWEEP_RESIDUAL, c->stream));
@@ -1198,7 +1234,8 @@ int calib_warm_start(calib_ctx* c, calib_mlp* mlp, const void* J_prev, const voi
     return CALIB_OK;
 }
 
-int calib_autotune(calib_ctx* c, int* split, int cap, int* cand, double* ms_per_lm_step, int* n_cand) {
+int calib_autotune(calib_ctx* c, int* split, int* split_trial, int cap, int* cand, double* ms_hessian,
+                   double* ms_trial, int* n_cand) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "set visibilities and coherencies first");
     if (c->formulation == 0 && c->ss_dirty) {
@@ -1210,11 +1247,13 @@ int calib_autotune(calib_ctx* c, int* split, int cap, int* cand, double* ms_per_
     tune_cache().clear();
     const int rc = autotune(c);
     if (rc) return rc;
-    if (split) *split = c->formulation == 0 ? c->ctas_per_sm : c->chunk_diags;
+    if (split) *split = c->formulation == 0 ? c->part_hv.m : c->chunk_diags;
+    if (split_trial) *split_trial = c->formulation == 0 ? c->part_tr.m : c->chunk_diags;
     const int n = (int)c->tune_log.size();
     for (int i = 0; i < n && i < cap; ++i) {
-        if (cand) cand[i] = c->tune_log[i].first;
-        if (ms_per_lm_step) ms_per_lm_step[i] = c->tune_log[i].second;
+        if (cand) cand[i] = c->tune_log[i].v;
+        if (ms_hessian) ms_hessian[i] = c->tune_log[i].hv;
+        if (ms_trial) ms_trial[i] = c->tune_log[i].tr;
     }
     if (n_cand) *n_cand = n;
     return CALIB_OK;
@@ -1232,7 +1271,7 @@ void calib_destroy(calib_ctx* c) {
                     (void*)c->evJ, (void*)c->evE, (void*)c->evOut, (void*)c->part, (void*)c->part_cost, (void*)c->part_dcost,
                     (void*)c->Z, (void*)c->Zprev, (void*)c->basis_d, (void*)c->Pinv_d, (void*)c->freqs_d,
                     (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->dual2, (void*)c->stats, (void*)c->iter_counter,
-                    (void*)c->status, (void*)c->pn_ss, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
+                    (void*)c->status, (void*)c->part_hv.pn, (void*)c->part_tr.pn, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
                     (void*)c->coh_off_d, c->staging, (void*)c->ws_prev, (void*)c->ws_mlp, (void*)c->ws_L,
                     (void*)c->xf_d, (void*)c->ws_chose})
         if (p) cudaFree(p);

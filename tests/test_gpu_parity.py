@@ -222,8 +222,9 @@ def test_autotuner_picks_a_measured_split_and_results_do_not_depend_on_it(lib):
     history with any fixed split agrees with the tuned one (only summation order changes)."""
     prob = CASES["ragged_n13_k3"]()
     cal = calibrator(lib, prob)
-    chosen, table = capi.calib_autotune(cal.ctx)
-    assert chosen in table and table[chosen] == min(table.values())
+    chosen, chosen_tr, table = capi.calib_autotune(cal.ctx)
+    assert chosen in table and table[chosen][0] == min(v[0] for v in table.values())
+    assert chosen_tr in table and table[chosen_tr][1] == min(v[1] for v in table.values())
     h_tuned = cal.iterate(3)
     for m in (1, 5):  # CTAs per SM of the statistics sweeps
         other = calibrator(lib, prob, ctas_per_sm=m)
