@@ -37,9 +37,9 @@ UNIT = "vis*dir*iter/s"
 
 # DRAM traffic per launch of each sweep kernel from one ncu capture; valid only for the kernel
 # source it was taken on (sha256 prefix of the kernel's .cu file), else reported as null.
-NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum, profiles/*_lofar_n62_k5.md
-    ("sweep_hessvec", "8e587c1134b3"): 269.0e6,
-    ("sweep_residual", "8e587c1134b3"): 468.0e6,
+NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_ss_sweep_lofar_n62_k5.md
+    ("stats_hessvec", "4bd60aef2d0b"): 83.8e6,
+    ("stats_trial", "4bd60aef2d0b"): 189.5e6,
 }
 KERNEL_SOURCE = {"sweep_residual": "sweep.cu", "sweep_hessvec": "sweep.cu",
                  "stats_hessvec": "ss.cu", "stats_trial": "ss.cu"}
@@ -342,7 +342,7 @@ def run_ours(args, world, rank, local):
                        ("ctas_per_sm" if args.formulation == "statistics" else "chunk_diagonals"): [split, split_tr],
                        "autotune_ms_hessian_trial": split_ms,
                        "step": "predict + cold start + 30 C-ADMM iterations",
-                       "l2": "inputs larger than L2 (436 MB per residual sweep, 242 MB per Hessian sweep)",
+                       "l2": "inputs larger than L2: every step streams the visibilities and predicted coherencies (436 MB) through predict, the statistics pass and the first residual sweep; each LM step reads U and S (169 MB)",
                        "parallelism": f"replica x{world}" if world > 1 else "single GPU",
                        "generate_s": round(t_gen, 2)},
             "roofline": roofline,
