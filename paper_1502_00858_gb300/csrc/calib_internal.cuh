@@ -109,7 +109,7 @@ struct ConsArgs {
     const float* rho;       // [K]
     AgentState* st;
     double* prim;           // [A][K] ||J_ik - B_i Z_k||
-    double* dual2;          // [I][K] ||Z_k^{n+1} - Z_k^n||^2
+    double* dual2;          // [I][K][8] per-CTA shares of ||Z_k^{n+1} - Z_k^n||^2
     double* stats;          // [max_iters][4]
     int* iter_counter;
     int A, I, P, M, N, K, max_iters;

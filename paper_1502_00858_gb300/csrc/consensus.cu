@@ -114,67 +114,98 @@ __global__ void __launch_bounds__(CT) k_gauge(const ConsArgs a) {
 }
 
 // Z_k = (1/rho_k) Pinv (sum_f b(f) (Y_fk + rho_k J_fk)) per interval, direction, station and entry
-// (Eq. Zest in the reshaped form z = vec(R P^T) of Section 3). One CTA per (interval, direction);
-// float64 accumulation. Also forms ||Z_k^{n+1} - Z_k^n||^2 for the dual residual (Section 4).
-__global__ void __launch_bounds__(CT) k_zupdate(const ConsArgs a) {
+// (Eq. Zest in the reshaped form z = vec(R P^T) of Section 3): one thread per (interval, direction,
+// station, entry), ZT of them per CTA; float64 accumulation over the P agents (frequencies). Also
+// this CTA's share of ||Z_k^{n+1} - Z_k^n||^2 for the dual residual (Section 4), written to its own
+// slot and summed in a fixed order by k_stats.
+constexpr int ZT = 128;
+constexpr int ZSLOTS = 8;  // CTAs per (interval, direction): 8N / ZT <= 8 for N <= 128
+
+__global__ void __launch_bounds__(ZT) k_zupdate(const ConsArgs a) {
     __shared__ double red[33];
     const int ivk = blockIdx.x;
     const int k = ivk % a.K, iv = ivk / a.K;
+    const int j = blockIdx.y * ZT + threadIdx.x;  // (station, entry) = (j / 8, j % 8)
+    const int NE = a.N * 8, M = a.M;
     const double rk = a.rho[k];
     double dz2 = 0.0;
-    for (int j = threadIdx.x; j < a.N * 8; j += blockDim.x) {
-        const int p = j / 8, e = j % 8;
+    if (j < NE) {
         double R[MAX_M];
-        for (int l = 0; l < a.M; ++l) R[l] = 0.0;
+#pragma unroll
+        for (int l = 0; l < MAX_M; ++l) R[l] = 0.0;
+        const size_t stride = (size_t)a.K * NE;  // next frequency, same direction
+        const size_t o0 = ((size_t)iv * a.P * a.K + k) * NE + j;
+#pragma unroll 4
         for (int f = 0; f < a.P; ++f) {
-            const size_t o = (((size_t)(iv * a.P + f) * a.K + k) * a.N + p) * 8 + e;
-            const double v = (double)a.Y[o] + rk * (double)a.J[o];
-            for (int l = 0; l < a.M; ++l) R[l] += a.basis[f * a.M + l] * v;
+            const size_t o = o0 + (size_t)f * stride;
+            const double v = (double)__ldg(a.Y + o) + rk * (double)__ldg(a.J + o);
+            const double* bf = a.basis + (size_t)f * M;
+#pragma unroll
+            for (int l = 0; l < MAX_M; ++l)
+                if (l < M) R[l] = fma(__ldg(bf + l), v, R[l]);
         }
-        for (int l = 0; l < a.M; ++l) {
+#pragma unroll
+        for (int l = 0; l < MAX_M; ++l) {
+            if (l >= M) continue;
             double z = 0.0;
-            for (int m = 0; m < a.M; ++m) z += a.Pinv[l * a.M + m] * R[m];
+#pragma unroll
+            for (int m = 0; m < MAX_M; ++m)
+                if (m < M) z = fma(__ldg(a.Pinv + l * M + m), R[m], z);
             z /= rk;
-            const size_t zo = ((((size_t)iv * a.K + k) * a.M + l) * a.N + p) * 8 + e;
+            const size_t zo = (((size_t)iv * a.K + k) * M + l) * NE + j;
             const double old = a.Z[zo];
             a.Zprev[zo] = old;
             a.Z[zo] = z;
-            dz2 += (z - old) * (z - old);
+            dz2 = fma(z - old, z - old, dz2);
         }
     }
     dz2 = bsum(dz2, red);
-    if (threadIdx.x == 0) a.dual2[ivk] = dz2;
+    if (threadIdx.x == 0) a.dual2[(size_t)ivk * ZSLOTS + blockIdx.y] = dz2;
 }
 
 // BZ_i = sum_l b_l(f_i) Z_l; Y_i += rho (J_i - BZ_i) (Eq. M3); per-agent ||J_ik - BZ_ik|| and
 // L_i(J_i, Z, Y_i) = g_i + Re tr(Y^H D) + rho/2 ||D||^2 with the new Y and BZ (Eq. sumtrace2).
+// One CTA per agent, one thread per (direction, station) block; the per-direction norms are summed
+// over the stations by one warp each (fixed order).
 __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) {
     __shared__ double red[33];
+    extern __shared__ double dds[];  // [K][N] ||J - BZ||^2 per block
     const int agent = blockIdx.x;
     const int iv = agent / a.P, f = agent - iv * a.P;
-    const int N = a.N;
+    const int N = a.N, KN = a.K * N, M = a.M;
+    double bl[MAX_M];
+#pragma unroll
+    for (int l = 0; l < MAX_M; ++l) bl[l] = l < M ? a.basis[f * M + l] : 0.0;
     double pen = 0.0;
-    for (int k = 0; k < a.K; ++k) {
+    for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) {
+        const int k = blk / N, p = blk - k * N;
         const double rk = a.rho[k];
+        const size_t o = ((size_t)agent * KN + blk) * 8;
+        const size_t zb = (((size_t)iv * a.K + k) * M * N + p) * 8;  // Z[iv][k][l][p][e] at l = 0
         double dd = 0.0;
-        for (int p = threadIdx.x; p < N; p += blockDim.x) {
-            const size_t o = (((size_t)agent * a.K + k) * N + p) * 8;
-            for (int e = 0; e < 8; ++e) {
-                double bz = 0.0;
-                for (int l = 0; l < a.M; ++l)
-                    bz += a.basis[f * a.M + l] * a.Z[((((size_t)iv * a.K + k) * a.M + l) * N + p) * 8 + e];
-                const double d = (double)a.J[o + e] - bz;
-                const float ynew = update_y ? (float)((double)a.Y[o + e] + rk * d) : a.Y[o + e];
-                a.Y[o + e] = ynew;
-                a.BZ[o + e] = (float)bz;
-                dd += d * d;
-                pen += (double)ynew * d + 0.5 * rk * d * d;
-            }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            double bz = 0.0;
+#pragma unroll
+            for (int l = 0; l < MAX_M; ++l)
+                if (l < M) bz = fma(bl[l], a.Z[zb + (size_t)l * N * 8 + e], bz);
+            const double d = (double)a.J[o + e] - bz;
+            const float ynew = update_y ? (float)((double)a.Y[o + e] + rk * d) : a.Y[o + e];
+            a.Y[o + e] = ynew;
+            a.BZ[o + e] = (float)bz;
+            dd = fma(d, d, dd);
+            pen += (double)ynew * d + 0.5 * rk * d * d;
         }
-        dd = bsum(dd, red);
-        if (threadIdx.x == 0 && a.prim) a.prim[(size_t)agent * a.K + k] = sqrt(dd);
+        dds[blk] = dd;
     }
-    pen = bsum(pen, red);
+    pen = bsum(pen, red);  // its barriers also publish dds
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < a.K; k += nw) {
+        double s = 0.0;
+        for (int p = lane; p < N; p += 32) s += dds[k * N + p];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && a.prim) a.prim[(size_t)agent * a.K + k] = sqrt(s);
+    }
     if (threadIdx.x == 0) a.st[agent].L = a.st[agent].g + pen;
 }
 
@@ -183,7 +214,12 @@ __global__ void __launch_bounds__(CT) k_stats(const ConsArgs a) {
     __shared__ double red[33];
     double prim = 0.0, dual = 0.0, obj = 0.0, g = 0.0;
     for (int i = threadIdx.x; i < a.A * a.K; i += blockDim.x) prim += a.prim[i];
-    for (int i = threadIdx.x; i < a.I * a.K; i += blockDim.x) dual += sqrt(a.dual2[i]);
+    const int zs = (a.N * 8 + ZT - 1) / ZT;  // Z-update CTAs per (interval, direction)
+    for (int i = threadIdx.x; i < a.I * a.K; i += blockDim.x) {
+        double d2 = 0.0;
+        for (int y = 0; y < zs; ++y) d2 += a.dual2[(size_t)i * ZSLOTS + y];
+        dual += sqrt(d2);
+    }
     for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
         obj += a.st[i].L;
         g += a.st[i].g;
@@ -220,15 +256,17 @@ cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_zupdate(const ConsArgs& a, cudaStream_t s) {
-    k_zupdate<<<a.I * a.K, CT, 0, s>>>(a);
+    const int zs = (a.N * 8 + ZT - 1) / ZT;
+    if (zs > ZSLOTS || a.M > MAX_M) return cudaErrorInvalidConfiguration;
+    k_zupdate<<<dim3(a.I * a.K, zs), ZT, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_yupdate(const ConsArgs& a, cudaStream_t s) {
-    k_yupdate<<<a.A, CT, 0, s>>>(a, 1);
+    k_yupdate<<<a.A, CT, (size_t)a.K * a.N * sizeof(double), s>>>(a, 1);
     return cudaGetLastError();
 }
 cudaError_t launch_bz_only(const ConsArgs& a, cudaStream_t s) {
-    k_yupdate<<<a.A, CT, 0, s>>>(a, 0);
+    k_yupdate<<<a.A, CT, (size_t)a.K * a.N * sizeof(double), s>>>(a, 0);
     return cudaGetLastError();
 }
 cudaError_t launch_stats(const ConsArgs& a, cudaStream_t s) {

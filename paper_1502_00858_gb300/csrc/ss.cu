@@ -125,12 +125,12 @@ __device__ __forceinline__ float2 shfl2x(float2 v) {
 __device__ __forceinline__ long long cta_of_item(long long i, long long W, long long G) { return ((i + 1) * G - 1) / W; }
 
 // KB: register bucket; EXACT: K == KB, so every loop bound and packed-S index is a constant.
-// SMALL: at most 128 threads (N <= 64). Register budgets: the Hessian pass fits 128 registers (4 CTAs
-// of 128 threads per SM); the trial pass holds three more per-direction arrays and gets 168 with
-// 128-thread CTAs (3 per SM, as many as its shared memory allows).
+// SMALL: at most 128 threads (N <= 64): 168 registers with 3 CTAs of 128 threads per SM (the trial
+// pass's shared memory allows 3; the Hessian pass spends the registers on loads hoisted ahead of
+// their use). Larger CTAs: 128 registers for the Hessian pass (2 CTAs of 256), unbounded for the trial.
 // Stage layout: [U: NP][K][2 rows] float4 (trial only) | [S: NP][KK] float2.
 template <int KB, bool HV, bool EXACT, bool SMALL>
-__global__ void __launch_bounds__((!HV && SMALL) ? 128 : 256, HV ? 2 : (SMALL ? 3 : 1))
+__global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? 3 : (HV ? 2 : 1))
     k_ss_sweep(const SSArgs a, const int stage_bytes) {
     constexpr int NST = nst<HV>();
     constexpr float sg = HV ? 1.f : -1.f;  // station terms: + in the Hessian pass, - (gradient) in the trial pass
@@ -365,8 +365,8 @@ cudaError_t prep_kb() {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, true, false>, attr, 200 * 1024);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, false, false>, attr, 200 * 1024);
-    if (e == cudaSuccess && !HV) e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, true, !HV>, attr, 200 * 1024);
-    if (e == cudaSuccess && !HV) e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, false, !HV>, attr, 200 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, true, true>, attr, 200 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, false, true>, attr, 200 * 1024);
     return e;
 }
 
@@ -387,13 +387,13 @@ cudaError_t prep_all() {
 
 template <int KB, bool HV>
 cudaError_t go(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
-    const bool exact = a.K == KB, small = !HV && threads <= 128;  // SMALL only matters for the trial pass
+    const bool exact = a.K == KB, small = threads <= 128;
     if (exact && small)
-        k_ss_sweep<KB, HV, true, !HV><<<grid, threads, smem, s>>>(a, sb);
+        k_ss_sweep<KB, HV, true, true><<<grid, threads, smem, s>>>(a, sb);
     else if (exact)
         k_ss_sweep<KB, HV, true, false><<<grid, threads, smem, s>>>(a, sb);
     else if (small)
-        k_ss_sweep<KB, HV, false, !HV><<<grid, threads, smem, s>>>(a, sb);
+        k_ss_sweep<KB, HV, false, true><<<grid, threads, smem, s>>>(a, sb);
     else
         k_ss_sweep<KB, HV, false, false><<<grid, threads, smem, s>>>(a, sb);
     return cudaGetLastError();
