@@ -172,9 +172,10 @@ int calib_hessvec(calib_ctx* ctx, const void* J, const void* eta, void* out, int
 int calib_sync(calib_ctx* ctx);
 
 /* Per-kernel timing over the following calib_admm_iter calls (CUDA events recorded
- * on the library stream around every launch of the sweep kernels when enabled). Kinds:
- * sweep_residual (direct residual/trial), sweep_hessvec (direct Hessian), stats_hessvec and
- * stats_trial (sufficient-statistics passes); bytes_per_launch and flops_per_launch are the
+ * on the library stream around every launch of the sweep and per-agent LM kernels when enabled).
+ * Kinds: sweep_residual (direct residual/trial), sweep_hessvec (direct Hessian), stats_hessvec and
+ * stats_trial (sufficient-statistics passes), pcg_step and lm_eval (per-agent LM kernels, no
+ * algorithmic byte or flop count: 0); bytes_per_launch and flops_per_launch are the
  * algorithmic bytes and real flops (complex multiply 6, complex multiply-add 8) of one launch.
  * Every output array may be NULL and receives up to cap entries; returns the number of kinds. */
 int calib_profile_enable(calib_ctx* ctx, int on);

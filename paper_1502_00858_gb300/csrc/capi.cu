@@ -126,8 +126,9 @@ struct calib_ctx {
     std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;
     long long launches = 0;
     bool profiling = false;
-    double prof_ms[4] = {0, 0, 0, 0};
-    long long prof_n[4] = {0, 0, 0, 0};
+    static constexpr int PROF_KINDS = 6;  // 4 sweep kinds, the PCG step, the LM evaluation
+    double prof_ms[PROF_KINDS] = {0, 0, 0, 0, 0, 0};
+    long long prof_n[PROF_KINDS] = {0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -464,16 +465,36 @@ struct Enq {
         if (err == cudaSuccess && e != cudaSuccess) err = e;
         ge->kernels += 1;
     }
-    void sweep(int mode, const float* J, const float* eta) {
+    // Profiling: CUDA events recorded around a launch of the given kind on the library stream.
+    ProfPair begin(int kind) {
         ProfPair pp{};
-        const bool prof = c->profiling;
-        const bool ss = c->formulation == 0 && mode != SWEEP_RESIDUAL;
-        if (prof) {
+        if (c->profiling) {
             cudaEventCreate(&pp.a);
             cudaEventCreate(&pp.b);
-            pp.kind = ss ? (mode == SWEEP_HESSVEC ? 2 : 3) : (mode == SWEEP_HESSVEC ? 1 : 0);
+            pp.kind = kind;
             cudaEventRecordWithFlags(pp.a, c->stream, cudaEventRecordExternal);
         }
+        return pp;
+    }
+    void end(ProfPair& pp) {
+        if (c->profiling) {
+            cudaEventRecordWithFlags(pp.b, c->stream, cudaEventRecordExternal);
+            ge->prof.push_back(pp);
+        }
+    }
+    void cg_step(const LMArgs& la, bool last) {
+        ProfPair pp = begin(4);
+        ok(launch_cg_step(la, last, c->stream));
+        end(pp);
+    }
+    void lm_eval(const LMArgs& la, int mode) {
+        ProfPair pp = begin(5);
+        ok(launch_lm_eval(la, mode, c->stream));
+        end(pp);
+    }
+    void sweep(int mode, const float* J, const float* eta) {
+        const bool ss = c->formulation == 0 && mode != SWEEP_RESIDUAL;
+        ProfPair pp = begin(ss ? (mode == SWEEP_HESSVEC ? 2 : 3) : (mode == SWEEP_HESSVEC ? 1 : 0));
         if (ss) {  // the statistics trial pass takes the trial point J' itself (written by the last PCG step)
             const float* e2 = mode == SWEEP_HESSVEC ? eta : c->Jt;
             const bool hv = mode == SWEEP_HESSVEC;
@@ -481,10 +502,7 @@ struct Enq {
         } else {
             ok(launch_sweep(sweep_args(c, mode, J, eta), mode, c->stream));
         }
-        if (prof) {
-            cudaEventRecordWithFlags(pp.b, c->stream, cudaEventRecordExternal);
-            ge->prof.push_back(pp);
-        }
+        end(pp);
     }
 };
 
@@ -496,17 +514,17 @@ void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
     const ConsArgs ca = cons_args(c);
     if (eval_first) {  // the residual sweep is the direct one in both formulations (it yields g exactly)
         q.sweep(SWEEP_RESIDUAL, c->J, nullptr);
-        q.ok(launch_lm_eval(lm_args(c, PARTS_DIRECT), LM_BEGIN_FROM_PARTIALS, c->stream));
+        q.lm_eval(lm_args(c, PARTS_DIRECT), LM_BEGIN_FROM_PARTIALS);
     } else {
-        q.ok(launch_lm_eval(la, LM_BEGIN_REUSE, c->stream));
+        q.lm_eval(la, LM_BEGIN_REUSE);
     }
     for (int l = 0; l < c->n_lm; ++l) {
         for (int k = 0; k < c->n_cg; ++k) {
             q.sweep(SWEEP_HESSVEC, c->J, c->p);
-            q.ok(launch_cg_step(la_hv, k == c->n_cg - 1, c->stream));  // the last one forms the trial point
+            q.cg_step(la_hv, k == c->n_cg - 1);  // the last one forms the trial point
         }
         q.sweep(SWEEP_TRIAL, c->J, c->x);
-        q.ok(launch_lm_eval(la, LM_ACCEPT, c->stream));
+        q.lm_eval(la, LM_ACCEPT);
     }
     if (gauge) q.ok(launch_gauge(ca, c->stream));
     q.ok(launch_zupdate(ca, c->stream));
@@ -1136,7 +1154,7 @@ int calib_sync(calib_ctx* c) {
 int calib_profile_enable(calib_ctx* c, int on) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     c->profiling = on != 0;
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < calib_ctx::PROF_KINDS; ++i) {
         c->prof_ms[i] = 0.0;
         c->prof_n[i] = 0;
     }
@@ -1146,15 +1164,16 @@ int calib_profile_enable(calib_ctx* c, int on) {
 int calib_profile_read(calib_ctx* c, int cap, const char** names, double* total_ms, long long* launches,
                        double* bytes_per_launch, double* flops_per_launch) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
-    static const char* kNames[4] = {"sweep_residual", "sweep_hessvec", "stats_hessvec", "stats_trial"};
-    for (int i = 0; i < 4 && i < cap; ++i) {
+    static const char* kNames[calib_ctx::PROF_KINDS] = {"sweep_residual", "sweep_hessvec", "stats_hessvec",
+                                                          "stats_trial", "pcg_step", "lm_eval"};
+    for (int i = 0; i < calib_ctx::PROF_KINDS && i < cap; ++i) {
         if (names) names[i] = kNames[i];
         if (total_ms) total_ms[i] = c->prof_ms[i];
         if (launches) launches[i] = c->prof_n[i];
-        if (bytes_per_launch) bytes_per_launch[i] = c->alg_bytes[i];
-        if (flops_per_launch) flops_per_launch[i] = c->alg_flops[i];
+        if (bytes_per_launch) bytes_per_launch[i] = i < 4 ? c->alg_bytes[i] : 0.0;
+        if (flops_per_launch) flops_per_launch[i] = i < 4 ? c->alg_flops[i] : 0.0;
     }
-    return 4;
+    return calib_ctx::PROF_KINDS;
 }
 
 long long calib_launch_count(calib_ctx* c) { return c ? c->launches : 0; }

@@ -511,37 +511,36 @@ __global__ void __launch_bounds__(LM_MAX_THREADS) k_cg_step(const LMArgs a, cons
     const int N = a.N, KN = a.K * N;
     const size_t off = (size_t)agent * KN * 8;
     AgentState& st = a.st[agent];
-    const int stop = a.timing ? 0 : st.cg_stop;
-    const float mu = a.timing ? 1.f : (float)st.mu;
-    const float rz = a.timing ? 1.f : (float)st.rz;
-    Blk x[BPT], r[BPT];
+    // Every load first, independent of the stop flag, so that they are in flight together.
+    Blk x[BPT], r[BPT], p[BPT], ap[BPT];  // ap holds the Hessian partial sum until it becomes A p
+    float lam[BPT], G[BPT][4];
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
         const int blk = tid + i * T;
-        x[i] = r[i] = zero_blk();
-        if (blk < KN) {
-            x[i] = ld_blk(a.x + off, blk);
-            r[i] = ld_blk(a.r + off, blk);
-        }
+        x[i] = r[i] = p[i] = ap[i] = zero_blk();
+        lam[i] = 0.f;
+        G[i][0] = G[i][1] = G[i][2] = G[i][3] = 0.f;
+        if (blk >= KN) continue;
+        x[i] = ld_blk(a.x + off, blk);
+        r[i] = ld_blk(a.r + off, blk);
+        p[i] = ld_blk(a.p + off, blk);
+        ap[i] = sum_parts(a, agent, blk, KN);
+        const float4 q = reinterpret_cast<const float4*>(a.Gm + (size_t)agent * KN * 4)[blk];
+        G[i][0] = q.x; G[i][1] = q.y; G[i][2] = q.z; G[i][3] = q.w;
+        lam[i] = 0.5f * a.rho[blk / N];
     }
+    const int stop = a.timing ? 0 : st.cg_stop;
+    const float mu = a.timing ? 1.f : (float)st.mu;
+    const float rz = a.timing ? 1.f : (float)st.rz;
     if (!stop) {
-        Blk p[BPT], ap[BPT];
-        float lam[BPT], G[BPT][4];
         float v[1] = {0.f};
 #pragma unroll
         for (int i = 0; i < BPT; ++i) {
             const int blk = tid + i * T;
-            p[i] = ap[i] = zero_blk();
-            lam[i] = 0.f;
-            G[i][0] = G[i][1] = G[i][2] = G[i][3] = 0.f;
             if (blk >= KN) continue;
-            lam[i] = 0.5f * a.rho[blk / N] + mu;
-            const Blk hp = sum_parts(a, agent, blk, KN);
-            p[i] = ld_blk(a.p + off, blk);
-            const float4 q = reinterpret_cast<const float4*>(a.Gm + (size_t)agent * KN * 4)[blk];
-            G[i][0] = q.x; G[i][1] = q.y; G[i][2] = q.z; G[i][3] = q.w;
+            lam[i] += mu;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) ap[i].v[e] = hp.v[e] + lam[i] * p[i].v[e];
+            for (int e = 0; e < 8; ++e) ap[i].v[e] = fmaf(lam[i], p[i].v[e], ap[i].v[e]);
             v[0] += dot8(p[i], ap[i]);
         }
         block_sum<1>(v, red[0]);
