@@ -175,7 +175,8 @@ int calib_sync(calib_ctx* ctx);
  * on the library stream around every launch of the sweep and per-agent LM kernels when enabled).
  * Kinds: sweep_residual (direct residual/trial), sweep_hessvec (direct Hessian), stats_hessvec and
  * stats_trial (sufficient-statistics passes), pcg_step and lm_eval (per-agent LM kernels, no
- * algorithmic byte or flop count: 0); bytes_per_launch and flops_per_launch are the
+ * algorithmic byte or flop count: 0), stats_pass (forming the statistics from V and C, timed
+ * outside the graph when calib_admm_iter runs it); bytes_per_launch and flops_per_launch are the
  * algorithmic bytes and real flops (complex multiply 6, complex multiply-add 8) of one launch.
  * Every output array may be NULL and receives up to cap entries; returns the number of kinds. */
 int calib_profile_enable(calib_ctx* ctx, int on);

@@ -162,9 +162,10 @@ cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s);
 cudaError_t launch_gram_weights(const float2* C, const DiagDesc* desc, const int* slot, const int* T, float* gw,
                                 int A, int D, int K, int N, cudaStream_t s);
 cudaError_t launch_check_finite(const float* x, long long n, int* status, cudaStream_t s);
-// Statistics into the full circulant layout (zero where flagged; clears U and S first).
+// Statistics into the full circulant layout (positions of flagged baselines are not written).
 cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc,
-                            const int* slot, const int* T, int A, int D, int K, int N, cudaStream_t s);
+                            const int* slot, const int* T, int A, int D, int K, int N, int Tmax, int* status,
+                            cudaStream_t s);
 
 // ---- launchers (ss.cu): sweeps on the sufficient statistics
 struct SSArgs {

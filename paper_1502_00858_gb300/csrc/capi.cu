@@ -76,6 +76,7 @@ struct calib_ctx {
     std::vector<double> freqs, basis, rho, Pinv;
     std::vector<float> rho_f;
     std::vector<int> T;
+    int Tmax = 1;  // largest samples per agent
     std::vector<long long> vis_off, coh_off;   // user layout offsets per agent (float2 units)
     long long user_v = 0, user_c = 0;           // user layout totals (float2)
 
@@ -84,8 +85,8 @@ struct calib_ctx {
     std::vector<int> slot_h, slot_b_h;
     long long int_v = 0, int_c = 0;             // internal totals (float2)
     long long int_u = 0, int_s = 0;             // sufficient-statistics totals (float2)
-    double alg_bytes[4] = {0, 0, 0, 0};         // algorithmic bytes per launch of each sweep kind
-    double alg_flops[4] = {0, 0, 0, 0};         // algorithmic real flops per launch of each sweep kind
+    double alg_bytes[7] = {0, 0, 0, 0, 0, 0, 0};  // algorithmic bytes per launch of each profiled kind
+    double alg_flops[7] = {0, 0, 0, 0, 0, 0, 0};  // algorithmic real flops per launch of each profiled kind
     std::vector<uint8_t> flags_h;
 
     // device
@@ -126,9 +127,9 @@ struct calib_ctx {
     std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;
     long long launches = 0;
     bool profiling = false;
-    static constexpr int PROF_KINDS = 6;  // 4 sweep kinds, the PCG step, the LM evaluation
-    double prof_ms[PROF_KINDS] = {0, 0, 0, 0, 0, 0};
-    long long prof_n[PROF_KINDS] = {0, 0, 0, 0, 0, 0};
+    static constexpr int PROF_KINDS = 7;  // 4 sweep kinds, the PCG step, the LM evaluation, the statistics pass
+    double prof_ms[PROF_KINDS] = {0, 0, 0, 0, 0, 0, 0};
+    long long prof_n[PROF_KINDS] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -329,6 +330,7 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     int smax = 4;
     double alg_res = 0, alg_hv = 0, alg_ssh = 0, alg_sst = 0;
     double flo[4] = {0, 0, 0, 0};
+    double alg_stp = 0, flo_stp = 0;
     for (int a = 0; a < A; ++a) {
         for (int d = 1; d <= D; ++d) {
             DiagDesc& dd = c->desc_h[(size_t)a * D + d - 1];
@@ -369,6 +371,10 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
             flo[1] += (double)n * (T * 64.0 * K + 120.0 * K + 128.0 * K);
             flo[2] += (double)n * (248.0 * K + 32.0 * K * K);
             flo[3] += (double)n * (432.0 * K + 64.0 * K * K);
+            // statistics pass: V and C of every sample read, U and S written; U: 4K and S: KK
+            // complex multiply-adds per sample
+            alg_stp += (double)n * (T * (32.0 + 8.0 * K) + 32.0 * K + 8.0 * KK);
+            flo_stp += (double)n * T * (32.0 * K + 8.0 * KK);
         }
     }
     c->int_v = voff;
@@ -385,6 +391,8 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     c->alg_bytes[2] = alg_ssh;
     c->alg_bytes[3] = alg_sst;
     for (int i = 0; i < 4; ++i) c->alg_flops[i] = flo[i];
+    c->alg_bytes[6] = alg_stp;
+    c->alg_flops[6] = flo_stp;
     c->TT_res = sweep_tile_samples(smax, K, false);
     c->TT_hv = sweep_tile_samples(smax, K, true);
     if (sweep_threads(smax) > 512) return fail(CALIB_EINVAL, "too many stations for one CTA per diagonal");
@@ -402,6 +410,9 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     CK(dalloc(&c->gw, (size_t)A * K * N * N));
     CK(dalloc(&c->ssU, (size_t)c->int_u));
     CK(dalloc(&c->ssS, (size_t)c->int_s));
+    // statistics of flagged baselines stay zero: the statistics pass never writes their positions
+    CK(cudaMemset(c->ssU, 0, (size_t)std::max(1LL, c->int_u) * sizeof(float2)));
+    CK(cudaMemset(c->ssS, 0, (size_t)std::max(1LL, c->int_s) * sizeof(float2)));
     CK(cudaMemcpy(c->desc, c->desc_h.data(), c->desc_h.size() * sizeof(DiagDesc), cudaMemcpyHostToDevice));
     if (!c->slot_h.empty()) {
         CK(cudaMemcpy(c->slot, c->slot_h.data(), c->slot_h.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -744,6 +755,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     for (int k = 0; k < K; ++k) c->rho_f[k] = (float)rho[k];
     c->Pinv = Pinv;
     c->T = T;
+    c->Tmax = *std::max_element(T.begin(), T.end());
     c->vis_off.resize(A);
     c->coh_off.resize(A);
     long long vo = 0, co = 0;
@@ -1018,7 +1030,23 @@ int calib_admm_iter(calib_ctx* c, int n_iters, calib_stats* hist) {
     CK(cudaMemsetAsync(c->iter_counter, 0, sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->status, 0, sizeof(int), c->stream));
     if (c->formulation == 0 && c->ss_dirty) {
-        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->slot, c->T_d, c->A, c->D, c->K, c->N, c->stream));
+        cudaEvent_t p0 = nullptr, p1 = nullptr;
+        if (c->profiling) {
+            CK(cudaEventCreate(&p0));
+            CK(cudaEventCreate(&p1));
+            CK(cudaEventRecord(p0, c->stream));
+        }
+        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->slot, c->T_d, c->A, c->D, c->K, c->N, c->Tmax, c->status, c->stream));
+        if (c->profiling) {
+            CK(cudaEventRecord(p1, c->stream));
+            CK(cudaEventSynchronize(p1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, p0, p1));
+            c->prof_ms[6] += ms;
+            c->prof_n[6] += 1;
+            cudaEventDestroy(p0);
+            cudaEventDestroy(p1);
+        }
         c->launches += 1;
         c->ss_dirty = false;
     }
@@ -1165,13 +1193,13 @@ int calib_profile_read(calib_ctx* c, int cap, const char** names, double* total_
                        double* bytes_per_launch, double* flops_per_launch) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     static const char* kNames[calib_ctx::PROF_KINDS] = {"sweep_residual", "sweep_hessvec", "stats_hessvec",
-                                                          "stats_trial", "pcg_step", "lm_eval"};
+                                                          "stats_trial", "pcg_step", "lm_eval", "stats_pass"};
     for (int i = 0; i < calib_ctx::PROF_KINDS && i < cap; ++i) {
         if (names) names[i] = kNames[i];
         if (total_ms) total_ms[i] = c->prof_ms[i];
         if (launches) launches[i] = c->prof_n[i];
-        if (bytes_per_launch) bytes_per_launch[i] = i < 4 ? c->alg_bytes[i] : 0.0;
-        if (flops_per_launch) flops_per_launch[i] = i < 4 ? c->alg_flops[i] : 0.0;
+        if (bytes_per_launch) bytes_per_launch[i] = c->alg_bytes[i];
+        if (flops_per_launch) flops_per_launch[i] = c->alg_flops[i];
     }
     return calib_ctx::PROF_KINDS;
 }
@@ -1258,7 +1286,7 @@ int calib_autotune(calib_ctx* c, int* split, int* split_trial, int cap, int* can
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "set visibilities and coherencies first");
     if (c->formulation == 0 && c->ss_dirty) {
-        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->slot, c->T_d, c->A, c->D, c->K, c->N, c->stream));
+        CK(launch_ss_stats(c->V, c->C, c->ssU, c->ssS, c->desc, c->slot, c->T_d, c->A, c->D, c->K, c->N, c->Tmax, c->status, c->stream));
         c->launches += 1;
         c->ss_dirty = false;
     }

@@ -11,7 +11,10 @@
 // before the float32 sincospi, so the phase error does not grow with baseline length.
 #include <math.h>
 
+#include <algorithm>
+
 #include "calib_internal.cuh"
+#include "tma.cuh"
 
 namespace calib {
 namespace {
@@ -163,49 +166,98 @@ __global__ void k_gram_weights(const float2* C, const DiagDesc* desc, const int*
     }
 }
 
-// Sufficient statistics per (agent, diagonal): thread (slot g, entry e) accumulates
-// U_k[e] = sum_t conj(c_tk) V_t[e] for all k, and its share of the packed S_kl = sum_t conj(c_tk) c_tl.
-// Written into the full circulant layout: compacted slot g goes to position i = its first station;
-// positions of flagged baselines keep the zeros the launcher cleared them to.
-__global__ void __launch_bounds__(256) k_ss_stats(const float2* V, const float2* C, float2* U, float2* S,
-                                                  const DiagDesc* desc, const int* slot, const int* T, int D,
-                                                  int K, int NP) {
+// Sufficient statistics per (agent, diagonal), one pass over its visibilities and coherencies:
+// U_k[e] = sum_t conj(c_tk) V_t[e] and the packed S_kl = sum_t conj(c_tk) c_tl (l >= k). Thread
+// (slot g, direction k) accumulates U_k (4 entries) and row k of S over the samples (the threads of
+// one slot share the loads of V_t and of the slot's K coherencies). STAGED: the CTA's whole V and C
+// block (contiguous, [T_a][n_pad][4] and [T_a][n_pad][K]) arrives in shared memory by two bulk
+// copies on one mbarrier, so every CTA has its bytes in flight at once; otherwise the samples are
+// read from global memory, two in flight per thread. Written into the full circulant layout:
+// compacted slot g goes to position i = its first station. Positions of flagged baselines are
+// never written (they hold the zeros set when the layout was built). KB >= K: register bucket.
+constexpr size_t SS_STATS_STAGED_MAX = 96 * 1024;  // shared memory of a staged CTA: at least two per SM
+
+template <int KB, bool STAGED>
+__global__ void __launch_bounds__(512, KB > 8 ? 1 : 2) k_ss_stats(const float2* __restrict__ V, const float2* __restrict__ C,
+                                                                   float2* __restrict__ U, float2* __restrict__ S,
+                                                                   const DiagDesc* desc, const int* slot, const int* T,
+                                                                   int D, int K, int NP, int* status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
     const int d = blockIdx.x, agent = blockIdx.y;
     const DiagDesc dsc = desc[(size_t)agent * D + d];
+    if (dsc.n == 0) return;
     const int Ta = T[agent];
     const int KK = K * (K + 1) / 2;
     const size_t blk = ((size_t)agent * D + d) * NP;  // first position of this (agent, diagonal)
-    for (int base = 0; base < dsc.n; base += blockDim.x / 4) {
-        const int g = base + (threadIdx.x >> 2), e = threadIdx.x & 3;
-        if (g >= dsc.n) continue;
+    const uint32_t vbytes = (uint32_t)Ta * dsc.n_pad * 32, cbytes = (uint32_t)Ta * dsc.n_pad * K * 8;
+    const float4* Vb = reinterpret_cast<const float4*>(V + dsc.voff);
+    const float2* Cb = C + dsc.coff;
+    if (STAGED) {
+        if (threadIdx.x == 0) {
+            mbar_init(&bar, 1);
+            fence_mbar_init();
+            mbar_expect_tx(&bar, vbytes + cbytes);
+            bulk_g2s(smem, Vb, vbytes, &bar);
+            bulk_g2s(smem + vbytes, Cb, cbytes, &bar);
+        }
+        __syncthreads();
+        const bool ok = mbar_wait_bounded(&bar, 0);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(status, STATUS_TIMEOUT);
+                mbar_wait_bounded(&bar, 0);  // the copies in flight still target this CTA's memory
+            }
+            return;
+        }
+        Vb = reinterpret_cast<const float4*>(smem);
+        Cb = reinterpret_cast<const float2*>(smem + vbytes);
+    }
+    auto ld4 = [](const float4* p) { return STAGED ? *p : __ldg(p); };
+    auto ld2 = [](const float2* p) { return STAGED ? *p : __ldg(p); };
+    for (int it = threadIdx.x; it < dsc.n * K; it += blockDim.x) {
+        const int g = it / K, k = it - g * K;
+        float2 u[4], srow[KB];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) u[e] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < KB; ++l) srow[l] = make_float2(0.f, 0.f);
+        const float4* vp = Vb + (size_t)g * 2;
+        const float2* cp = Cb + (size_t)g * K;
+        const size_t vstride = (size_t)dsc.n_pad * 2, cstride = (size_t)dsc.n_pad * K;
+        auto accumulate = [&](float4 v0, float4 v1, const float2* c) {
+            const float2 ck = ld2(c + k);
+            const float2 vv[4] = {make_float2(v0.x, v0.y), make_float2(v0.z, v0.w), make_float2(v1.x, v1.y),
+                                  make_float2(v1.z, v1.w)};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {  // conj(c_k) V
+                u[e].x = fmaf(ck.x, vv[e].x, fmaf(ck.y, vv[e].y, u[e].x));
+                u[e].y = fmaf(ck.x, vv[e].y, fmaf(-ck.y, vv[e].x, u[e].y));
+            }
+#pragma unroll
+            for (int l = 0; l < KB; ++l) {  // conj(c_k) c_l, l >= k
+                if (l < k || l >= K) continue;
+                const float2 cl = ld2(c + l);
+                srow[l].x = fmaf(ck.x, cl.x, fmaf(ck.y, cl.y, srow[l].x));
+                srow[l].y = fmaf(ck.x, cl.y, fmaf(-ck.y, cl.x, srow[l].y));
+            }
+        };
+        int t = 0;
+        for (; t + 1 < Ta; t += 2) {
+            const float4 a0 = ld4(vp + t * vstride), a1 = ld4(vp + t * vstride + 1);
+            const float4 b0 = ld4(vp + (t + 1) * vstride), b1 = ld4(vp + (t + 1) * vstride + 1);
+            accumulate(a0, a1, cp + t * cstride);
+            accumulate(b0, b1, cp + (t + 1) * cstride);
+        }
+        if (t < Ta) accumulate(ld4(vp + t * vstride), ld4(vp + t * vstride + 1), cp + t * cstride);
         const size_t pos = blk + (slot[dsc.slot_off + g] & 0xff);
-        float2 u[MAX_K];
-        for (int k = 0; k < K; ++k) u[k] = make_float2(0.f, 0.f);
-        for (int t = 0; t < Ta; ++t) {
-            const float2 v = V[dsc.voff + ((size_t)t * dsc.n_pad + g) * 4 + e];
-            const float2* cp = C + dsc.coff + ((size_t)t * dsc.n_pad + g) * K;
-            for (int k = 0; k < K; ++k) {
-                const float2 c = cp[k];
-                u[k].x = fmaf(c.x, v.x, fmaf(c.y, v.y, u[k].x));
-                u[k].y = fmaf(c.x, v.y, fmaf(-c.y, v.x, u[k].y));
-            }
-        }
-        float2* uo = U + pos * K * 4;
-        for (int k = 0; k < K; ++k) uo[k * 4 + e] = u[k];
-        // packed S entries idx = e, e + 4, ...
-        for (int idx = e; idx < KK; idx += 4) {
-            int k = 0, rem = idx;
-            while (rem >= K - k) { rem -= K - k; ++k; }
-            const int l = k + rem;
-            float sr = 0.f, si = 0.f;
-            for (int t = 0; t < Ta; ++t) {
-                const float2* cp = C + dsc.coff + ((size_t)t * dsc.n_pad + g) * K;
-                const float2 ck = cp[k], cl = cp[l];
-                sr = fmaf(ck.x, cl.x, fmaf(ck.y, cl.y, sr));   // conj(c_k) c_l
-                si = fmaf(ck.x, cl.y, fmaf(-ck.y, cl.x, si));
-            }
-            S[pos * KK + idx] = make_float2(sr, si);
-        }
+        float4* uo = reinterpret_cast<float4*>(U + (pos * K + k) * 4);
+        uo[0] = make_float4(u[0].x, u[0].y, u[1].x, u[1].y);
+        uo[1] = make_float4(u[2].x, u[2].y, u[3].x, u[3].y);
+        float2* so = S + pos * KK + (size_t)k * K - k * (k - 1) / 2;  // entry (k, l) at so[l - k]
+#pragma unroll
+        for (int l = 0; l < KB; ++l)
+            if (l >= k && l < K) so[l - k] = srow[l];
     }
 }
 
@@ -220,7 +272,13 @@ __global__ void k_check_finite(const float* x, long long n, int* status) {
 }  // namespace
 
 cudaError_t prepare_data_kernels() {
-    return cudaFuncSetAttribute(k_predict, cudaFuncAttributeMaxDynamicSharedMemorySize, 100 * 1024);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    const int st = (int)SS_STATS_STAGED_MAX;
+    cudaError_t e = cudaFuncSetAttribute(k_predict, attr, 100 * 1024);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ss_stats<4, true>, attr, st);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ss_stats<8, true>, attr, st);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ss_stats<MAX_K, true>, attr, st);
+    return e;
 }
 
 cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t s) {
@@ -247,16 +305,29 @@ cudaError_t launch_gram_weights(const float2* C, const DiagDesc* desc, const int
     k_gram_weights<<<A, 256, 0, s>>>(C, desc, slot, T, gw, D, K, N);
     return cudaGetLastError();
 }
-cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc,
-                            const int* slot, const int* T, int A, int D, int K, int N, cudaStream_t s) {
-    const int NP = (N + 3) / 4 * 4, KK = K * (K + 1) / 2;
-    const size_t pos = (size_t)A * D * NP;
-    cudaError_t e = cudaMemsetAsync(U, 0, pos * K * 4 * sizeof(float2), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(S, 0, pos * KK * sizeof(float2), s);
-    if (e != cudaSuccess) return e;
+// Shared memory of a CTA of the staged statistics pass: the largest V + C block.
+size_t ss_stats_smem(int N, int K, int Tmax) { return (size_t)Tmax * ((N + 3) / 4 * 4) * (32 + 8 * K); }
+
+template <int KB>
+cudaError_t ss_stats_go(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc, const int* slot,
+                        const int* T, int A, int D, int K, int NP, size_t smem, int* status, cudaStream_t s) {
+    const int threads = std::min(512, ((NP * K + 31) / 32) * 32);
     dim3 grid(D, A);
-    k_ss_stats<<<grid, 256, 0, s>>>(V, C, U, S, desc, slot, T, D, K, NP);
+    if (smem <= SS_STATS_STAGED_MAX)
+        k_ss_stats<KB, true><<<grid, threads, smem, s>>>(V, C, U, S, desc, slot, T, D, K, NP, status);
+    else
+        k_ss_stats<KB, false><<<grid, threads, 0, s>>>(V, C, U, S, desc, slot, T, D, K, NP, status);
     return cudaGetLastError();
+}
+
+cudaError_t launch_ss_stats(const float2* V, const float2* C, float2* U, float2* S, const DiagDesc* desc,
+                            const int* slot, const int* T, int A, int D, int K, int N, int Tmax, int* status,
+                            cudaStream_t s) {
+    const int NP = (N + 3) / 4 * 4;
+    const size_t smem = ss_stats_smem(N, K, Tmax);
+    if (K <= 4) return ss_stats_go<4>(V, C, U, S, desc, slot, T, A, D, K, NP, smem, status, s);
+    if (K <= 8) return ss_stats_go<8>(V, C, U, S, desc, slot, T, A, D, K, NP, smem, status, s);
+    return ss_stats_go<MAX_K>(V, C, U, S, desc, slot, T, A, D, K, NP, smem, status, s);
 }
 
 cudaError_t launch_check_finite(const float* x, long long n, int* status, cudaStream_t s) {
