@@ -30,9 +30,14 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "lofar_n62_k5"
+WORKLOAD = "lofar_n62_k5"  # the default workload; --workload picks another
 N_LM, N_CG = 10, 4
-METRIC = "ADMM vis*dir*iter/s (LOFAR-shaped: N=62, K=5, 32 subbands, 10 intervals x 10 samples)"
+METRICS = {
+    "lofar_n62_k5": "ADMM vis*dir*iter/s (LOFAR-shaped: N=62, K=5, 32 subbands, 10 intervals x 10 samples)",
+    "uneven_n62_k10": "ADMM vis*dir*iter/s (batched uneven: N=62, K=10, 256 subbands x 10 intervals, "
+                      "5/10/20 samples per subband, 0-15 % of baselines flagged)",
+}
+METRIC = METRICS[WORKLOAD]
 UNIT = "vis*dir*iter/s"
 
 # DRAM traffic per launch of each sweep kernel from one ncu capture; valid only for the kernel
@@ -135,8 +140,10 @@ def oracle_sample(prob, n_freq: int):
     subbands (same per-agent data, same LM/PCG schedule). Returns (seconds, vis*dir*iter)."""
     from oracle import admm as O
 
+    up = (lambda xs: [np.asarray(x, dtype=np.complex128) for x in xs]) if isinstance(prob["V"], list) else \
+        (lambda xs: np.asarray(xs, dtype=np.complex128))
     sub = dict(prob, P=n_freq, I=1, A=n_freq, basis=prob["basis"][:n_freq], freqs=prob["freqs"][:n_freq],
-               V=prob["V"][:n_freq], C=prob["C"][:n_freq], flags=prob["flags"][:n_freq], T=prob["T"][:n_freq])
+               V=up(prob["V"][:n_freq]), C=up(prob["C"][:n_freq]), flags=prob["flags"][:n_freq], T=prob["T"][:n_freq])
     t0 = time.perf_counter()
     O.admm(sub, 1, n_lm=N_LM, n_cg=N_CG)
     dt = time.perf_counter() - t0
@@ -152,7 +159,7 @@ def run_reference(args, world, rank):
         return
     from synth import make_problem
 
-    prob = make_problem(WORKLOAD, I=1)
+    prob = make_problem(args.workload, I=1)
     n_freq = 4
     for _ in range(args.warmup):
         oracle_sample(prob, n_freq)
@@ -162,12 +169,12 @@ def run_reference(args, world, rank):
         tot_t += dt
         tot_u += u
     value = tot_u / tot_t
-    sample = f"one C-ADMM iteration (10 LM x 4 PCG) of interval 0, first {n_freq} of 32 subbands, per step"
+    sample = f"one C-ADMM iteration (10 LM x 4 PCG) of interval 0, first {n_freq} of {prob['P']} subbands, per step"
     print(json.dumps({
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_lm": N_LM, "n_cg": N_CG, "sample": sample},
+        "config": {"workload": args.workload, "n_lm": N_LM, "n_cg": N_CG, "sample": sample},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -188,7 +195,9 @@ def run_ours(args, world, rank, local):
     capi.load()
 
     t_gen = time.perf_counter()
-    prob = make_problem(WORKLOAD, seed=1 + rank)
+    # the large uneven batch is generated in complex64 (its visibilities and coherencies take 6.4 GB)
+    gen_kw = {"dtype": np.complex64} if args.workload != WORKLOAD else {}
+    prob = make_problem(args.workload, seed=1 + rank, **gen_kw)
     ul = user_layout(prob)
     t_gen = time.perf_counter() - t_gen
     n_admm = prob["n_admm"]
@@ -338,22 +347,27 @@ def run_ours(args, world, rank, local):
         n_freq = 8
         cdt, cu = oracle_sample(prob, n_freq)
         cpu = {"value": cu / cdt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"one C-ADMM iteration (10 LM x 4 PCG) of interval 0, first {n_freq} of 32 subbands "
-                         f"({cdt:.1f} s)"}
+               "sample": f"one C-ADMM iteration (10 LM x 4 PCG) of interval 0, first {n_freq} of {prob['P']} "
+                         f"subbands ({cdt:.1f} s)"}
 
     if rank == 0:
         out = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "stations": prob["N"], "baselines": prob["B"], "directions": prob["K"],
-                       "subbands": prob["P"], "intervals": prob["I"], "samples": 10, "admm_iters": n_admm,
+            "config": {"workload": args.workload, "stations": prob["N"], "baselines": prob["B"], "directions": prob["K"],
+                       "subbands": prob["P"], "intervals": prob["I"],
+                       "samples": sorted(set(int(t) for t in np.asarray(prob["T"]).ravel())),
+                       "flagged_fraction": round(float(np.mean(prob["flags"])), 4), "admm_iters": n_admm,
                        "n_lm": N_LM, "n_cg": N_CG, "basis": "Bernstein degree 3", "rho": 10.0,
                        "formulation": args.formulation,
                        ("ctas_per_sm" if args.formulation == "statistics" else "chunk_diagonals"): [split, split_tr],
                        "autotune_ms_hessian_trial": split_ms,
-                       "step": "predict + cold start + 30 C-ADMM iterations",
-                       "l2": "inputs larger than L2: every step streams the visibilities and predicted coherencies (436 MB) through predict, the statistics pass and the first residual sweep; each LM step reads U and S (169 MB)",
+                       "step": f"predict + cold start + {n_admm} C-ADMM iterations",
+                       "l2": f"inputs larger than L2: every step streams the visibilities and predicted coherencies "
+                             f"({(ul['vis'].nbytes + ul['coh'].nbytes) / 1e6:.0f} MB) through predict, the statistics "
+                             f"pass and the first residual sweep; each LM step reads U and S "
+                             f"({1e-6 * prof['stats_trial']['bytes_per_launch']:.0f} MB)",
                        "parallelism": f"replica x{world}" if world > 1 else "single GPU",
                        "generate_s": round(t_gen, 2)},
             "roofline": roofline,
@@ -377,6 +391,7 @@ def main():
     ap.add_argument("--chunk-diagonals", type=int, default=0, help="direct sweeps: diagonals per CTA (0 = tuned)")
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="statistics sweeps: CTAs per SM (0 = tuned)")
     ap.add_argument("--formulation", choices=["statistics", "direct"], default="statistics")
+    ap.add_argument("--workload", choices=sorted(METRICS), default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run one launch of each sweep on the workload and exit (profiler captures)")

@@ -175,7 +175,9 @@ __global__ void k_gram_weights(const float2* C, const DiagDesc* desc, const int*
 // read from global memory, two in flight per thread. Written into the full circulant layout:
 // compacted slot g goes to position i = its first station. Positions of flagged baselines are
 // never written (they hold the zeros set when the layout was built). KB >= K: register bucket.
-constexpr size_t SS_STATS_STAGED_MAX = 96 * 1024;  // shared memory of a staged CTA: at least two per SM
+// Largest V + C block staged whole in shared memory; even one CTA per SM keeps far more bytes in
+// flight than the streaming loop.
+constexpr size_t SS_STATS_STAGED_MAX = 200 * 1024;
 
 template <int KB, bool STAGED>
 __global__ void __launch_bounds__(512, KB > 8 ? 1 : 2) k_ss_stats(const float2* __restrict__ V, const float2* __restrict__ C,

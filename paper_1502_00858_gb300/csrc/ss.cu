@@ -92,10 +92,11 @@ __device__ __forceinline__ long long cta_of_item(long long i, long long W, long 
 // KB: register bucket; EXACT: K == KB, so every loop bound and packed-S index is a constant.
 // SMALL: at most 128 threads (N <= 64): 168 registers with 3 CTAs of 128 threads per SM (the trial
 // pass's shared memory allows 3; the Hessian pass spends the registers on loads hoisted ahead of
-// their use). Larger CTAs: 128 registers for the Hessian pass (2 CTAs of 256), unbounded for the trial.
+// their use); from K = 8 on, shared memory allows 2 CTAs (K = 8) or 1 (K >= 10) and the register
+// budget follows. Larger CTAs: 128 registers for the Hessian pass (2 CTAs of 256), unbounded for the trial.
 // Stage layout: [U: NP][K][2 rows] float4 (trial only) | [S: NP][KK] float2.
 template <int KB, bool HV, bool EXACT, bool SMALL>
-__global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? 3 : (HV ? 2 : 1))
+__global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB >= 8 ? 2 : 3)) : (HV ? 2 : 1))
     k_ss_sweep(const SSArgs a, const int stage_bytes) {
     constexpr int NST = nst<HV>();
     constexpr float sg = HV ? 1.f : -1.f;  // station terms: + in the Hessian pass, - (gradient) in the trial pass
