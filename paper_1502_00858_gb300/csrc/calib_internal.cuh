@@ -3,8 +3,9 @@
 // Device data layout (all float32 unless noted; "block" = one 2x2 complex matrix = 8 floats):
 //   J, Jt, Y, BZ, gradg, grad, x, r, p   [A][K][N][8]
 //   Gm        [A][K][N][4]   Jacobi blocks G_pk (Hermitian): g00, g11, re g01, im g01
-//   gw        [A][K][N][N]   Jacobi weights: gw[a][k][o][p] = s_bk = sum_t |c_btk|^2 of the baseline
-//                            b = (p, o) (0 where flagged or o = p); G_pk = sum_o gw[a][k][o][p] J_ok^H J_ok
+//   gw        [A][K][N][NW]  Jacobi weights, rows padded to NW = roundup(N, 4) with zeros:
+//                            gw[a][k][p][o] = s_bk = sum_t |c_btk|^2 of the baseline b = (p, o) (symmetric;
+//                            0 where flagged or o = p); G_pk = sum_o gw[a][k][p][o] J_ok^H J_ok
 //   part      [A][stride][K][N][8]  partial station sums of a baseline sweep (per chunk for the direct
 //                                   sweeps, per (agent, CTA) piece for the statistics sweeps)
 //   part_cost [A][stride]  float64 partial data cost
@@ -92,7 +93,7 @@ struct LMArgs {
     float* J; float* Jt; const float* Y; const float* BZ;
     float* gradg; float* grad; float* x; float* r; float* p;
     float* Gm;
-    const float* gw;        // [A][K][N][N] Jacobi weights
+    const float* gw;        // [A][K][N][NW] Jacobi weights, NW = roundup(N, 4)
     AgentState* st;
     const float* rho;       // [K]
     int A, N, K, D;

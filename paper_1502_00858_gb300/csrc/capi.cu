@@ -407,7 +407,7 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     CK(dalloc(&c->desc, c->desc_h.size()));
     CK(dalloc(&c->slot, c->slot_h.size()));
     CK(dalloc(&c->slot_b, c->slot_b_h.size()));
-    CK(dalloc(&c->gw, (size_t)A * K * N * N));
+    CK(dalloc(&c->gw, (size_t)A * K * N * ((N + 3) / 4 * 4)));
     CK(dalloc(&c->ssU, (size_t)c->int_u));
     CK(dalloc(&c->ssS, (size_t)c->int_s));
     // statistics of flagged baselines stay zero: the statistics pass never writes their positions

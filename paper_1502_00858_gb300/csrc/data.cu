@@ -145,8 +145,9 @@ __global__ void __launch_bounds__(256) k_predict(const PredictArgs a, int s_chun
 __global__ void k_gram_weights(const float2* C, const DiagDesc* desc, const int* slot, const int* T, float* gw,
                                int D, int K, int N) {
     const int agent = blockIdx.x;
-    float* W = gw + (size_t)agent * K * N * N;
-    for (int i = threadIdx.x; i < K * N * N; i += blockDim.x) W[i] = 0.f;
+    const int NW = (N + 3) / 4 * 4;  // row stride: 16-byte rows
+    float* W = gw + (size_t)agent * K * N * NW;
+    for (int i = threadIdx.x; i < K * N * NW; i += blockDim.x) W[i] = 0.f;
     __syncthreads();
     const int Ta = T[agent];
     for (int d = 0; d < D; ++d) {
@@ -160,8 +161,8 @@ __global__ void k_gram_weights(const float2* C, const DiagDesc* desc, const int*
             }
             const int sl = slot[dsc.slot_off + g];
             const int f = sl & 0xff, sc = (sl >> 8) & 0xff;
-            W[((size_t)k * N + f) * N + sc] = s;
-            W[((size_t)k * N + sc) * N + f] = s;
+            W[((size_t)k * N + f) * NW + sc] = s;
+            W[((size_t)k * N + sc) * NW + f] = s;
         }
     }
 }

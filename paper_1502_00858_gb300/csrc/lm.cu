@@ -27,6 +27,9 @@
 namespace calib {
 namespace {
 
+// At most 512 threads a CTA. With one block per thread (K*N <= 512) at most 64 registers a thread,
+// so that 3 agents' CTAs share an SM (320 agents of 320 threads fit 152 SMs in one wave); larger
+// K*N keeps its blocks in registers instead.
 constexpr int LM_MAX_THREADS = 512;
 
 struct Blk { float v[8]; };
@@ -290,7 +293,8 @@ __device__ void project_out_gauge(const Blk (&j)[BPT], Blk (&g)[BPT], int K, int
 }
 
 // Jacobi blocks G_pk = sum_o s_(p,o)k J_ok^H J_ok at the CTA's J (held by the threads), from the
-// dense weights gw (coalesced across p) and the products J_ok^H J_ok staged in sm (KN*4 floats).
+// dense weights gw (thread (k, p) reads its 16-byte aligned row, all loads independent) and the
+// products J_ok^H J_ok staged in sm (KN*4 floats).
 template <int BPT>
 __device__ void gram_blocks(const LMArgs& a, int agent, const Blk (&j)[BPT], float* sm, float (&G)[BPT][4]) {
     const int T = blockDim.x, N = a.N, K = a.K, KN = K * N;
@@ -313,17 +317,24 @@ __device__ void gram_blocks(const LMArgs& a, int agent, const Blk (&j)[BPT], flo
         G[i][0] = G[i][1] = G[i][2] = G[i][3] = 0.f;
         if (blk >= KN) continue;
         const int k = blk / N, p = blk - k * N;
-        const float* W = a.gw + ((size_t)agent * K + k) * N * N + p;
+        const int NW4 = (N + 3) / 4;
+        const float4* W = reinterpret_cast<const float4*>(a.gw + (((size_t)agent * K + k) * N + p) * NW4 * 4);
         const float4* X = reinterpret_cast<const float4*>(sm) + k * N;
         float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
-#pragma unroll 8
-        for (int o = 0; o < N; ++o) {
-            const float w = __ldg(W + (size_t)o * N);
-            const float4 x = X[o];
-            g0 = fmaf(w, x.x, g0);
-            g1 = fmaf(w, x.y, g1);
-            g2 = fmaf(w, x.z, g2);
-            g3 = fmaf(w, x.w, g3);
+#pragma unroll 16
+        for (int o4 = 0; o4 < NW4; ++o4) {
+            const float4 w4 = __ldg(W + o4);
+            const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int o = 4 * o4 + q;
+                if (o >= N) break;  // row padding
+                const float4 x = X[o];
+                g0 = fmaf(wv[q], x.x, g0);
+                g1 = fmaf(wv[q], x.y, g1);
+                g2 = fmaf(wv[q], x.z, g2);
+                g3 = fmaf(wv[q], x.w, g3);
+            }
         }
         G[i][0] = g0; G[i][1] = g1; G[i][2] = g2; G[i][3] = g3;
         reinterpret_cast<float4*>(a.Gm + (size_t)agent * KN * 4)[blk] = make_float4(g0, g1, g2, g3);
@@ -336,7 +347,7 @@ __device__ void gram_blocks(const LMArgs& a, int agent, const Blk (&j)[BPT], flo
 // PCG initialisation for the next LM step: grad = gradg + Y/2 + rho/2 (J - BZ), r = -grad,
 // p = z = M^-1 r, x = 0, rz = h(r, z).
 template <int BPT>
-__global__ void __launch_bounds__(LM_MAX_THREADS) k_lm_eval(const LMArgs a, const int mode) {
+__global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_lm_eval(const LMArgs a, const int mode) {
     extern __shared__ __align__(16) float sm[];  // KN*GT floats (gauge terms), reused for J^H J
     __shared__ float red[4][64];
     __shared__ float Asol[MAX_K * 4];
@@ -505,7 +516,7 @@ __global__ void __launch_bounds__(LM_MAX_THREADS) k_lm_eval(const LMArgs a, cons
 // One PCG step of one agent after the Hessian sweep of its direction p; with last set, also the
 // LM trial point Jt = J + x and the predicted decrease pred = 1/2 h(x, b + r) + mu/2 h(x, x).
 template <int BPT>
-__global__ void __launch_bounds__(LM_MAX_THREADS) k_cg_step(const LMArgs a, const int last) {
+__global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_cg_step(const LMArgs a, const int last) {
     __shared__ float red[3][64];
     const int agent = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
     const int N = a.N, KN = a.K * N;
