@@ -65,6 +65,13 @@ CASES = {
     "ragged_n13_k3": ragged_problem,
     "n2_single_baseline": lambda: make_problem("tiny_n8_k1", N=2, P=3, seed=7),
     "n3_k2": lambda: make_problem("adjoint_n16_k3", N=3, K=2, P=4, I=1, T=1, seed=8),
+    # ten directions (the batched workload's K: exact register bucket, shared-memory-limited sweeps)
+    "n10_k10_flagged": lambda: make_problem("adjoint_n16_k3", N=10, K=10, P=4, I=1, T=(2, 3), flag_max=0.1, seed=21),
+    # seven directions: a register bucket larger than K
+    "n9_k7": lambda: make_problem("adjoint_n16_k3", N=9, K=7, P=4, I=1, T=2, seed=22),
+    # 700 samples per interval: the statistics pass's per-(agent, diagonal) block exceeds what it
+    # stages in shared memory and it reads global memory directly
+    "n8_t700": lambda: make_problem("tiny_n8_k1", N=8, P=3, T=700, seed=23),
 }
 
 
@@ -154,7 +161,8 @@ def run_both(lib, prob, n_iter, n_lm=10, n_cg=4, form="statistics"):
 
 
 @pytest.mark.parametrize("form", sorted(FORMS))
-@pytest.mark.parametrize("case", ["tiny_n8_k1", "ragged_n13_k3", "n2_single_baseline"])
+@pytest.mark.parametrize("case", ["tiny_n8_k1", "ragged_n13_k3", "n2_single_baseline", "n10_k10_flagged", "n9_k7",
+                                  "n8_t700"])
 def test_admm_history_matches_oracle(lib, case, form):
     prob = CASES[case]()
     n_iter = 10 if case == "tiny_n8_k1" else 4
