@@ -129,6 +129,23 @@ def dist_setup():
     return world, rank, local
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of each rank's value (the slowest rank's time); a collective when world > 1."""
+    if world == 1:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_step_per_rank: float, steps: int, dt_slowest: float) -> float:
+    """Whole-job throughput: every rank processes its own batch (weak scaling), the job takes as
+    long as the slowest rank."""
+    return world * units_per_step_per_rank * steps / dt_slowest
+
+
 def units(prob) -> float:
     """Unflagged visibilities x directions per ADMM iteration."""
     keep = (prob["flags"] == 0).sum(axis=1)
@@ -265,11 +282,8 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop()
     dt = ev0.elapsed_time(ev1) / 1e3
     launches = capi.calib_launch_count(cal.ctx) - launches0
-    if world > 1:
-        t = torch.tensor([dt], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        dt = float(t.item())
-    value = world * per_iter_units * n_admm * args.steps / dt
+    dt = max_over_ranks(dt, world, dev)
+    value = whole_job_rate(world, per_iter_units * n_admm, args.steps, dt)
 
     # per-kernel durations (CUDA events recorded on the library stream around every sweep launch)
     capi.calib_profile_enable(cal.ctx, True)
@@ -335,11 +349,8 @@ def run_ours(args, world, rank, local):
         e2e_step()
     torch.cuda.synchronize()
     e2e_dt = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_dt], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_dt = float(t.item())
-    e2e_value = world * per_iter_units * n_admm * args.steps / e2e_dt
+    e2e_dt = max_over_ranks(e2e_dt, world, dev)
+    e2e_value = whole_job_rate(world, per_iter_units * n_admm, args.steps, e2e_dt)
     h2d = vis_h.numel() * 4 + uvw_h.numel() * 8 + sky_h.numel() * 8
     d2h = J_h.numel() * 4
 
