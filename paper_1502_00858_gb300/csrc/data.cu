@@ -80,27 +80,34 @@ __global__ void __launch_bounds__(256) k_predict(const PredictArgs a, int s_chun
     const int iv = agent / a.P, fi = agent - iv * a.P;
     const double f = a.freqs[fi];
     const int N = a.N, K = a.K;
-    float2* E = reinterpret_cast<float2*>(smem);                          // [K][s_chunk][N]
+    double* lmn = reinterpret_cast<double*>(smem);                        // [K][s_chunk][3] l, m, n - 1
+    float2* E = reinterpret_cast<float2*>(lmn + (size_t)K * s_chunk * 3);  // [K][s_chunk][N]
     float* flux = reinterpret_cast<float*>(E + (size_t)K * s_chunk * N);  // [K][s_chunk]
     const double* uvw = a.uvw + (((size_t)iv * a.Tmax + t) * N) * 3;
     const DiagDesc* dsc_agent = a.desc + (size_t)agent * a.D;
 
     for (int s0 = 0; s0 < a.S; s0 += s_chunk) {
         const int ns = min(s_chunk, a.S - s0);
+        // per source: flux at f and its direction (l, m, n - 1), scaled by f / c
+        const double fc = f / C_LIGHT;
         for (int i = threadIdx.x; i < K * ns; i += blockDim.x) {
             const int k = i / ns, s = i - k * ns;
             const double* src = a.sky + ((size_t)k * a.S + s0 + s) * 4;
             flux[k * s_chunk + s] = (float)(src[2] * pow(f / a.f0, src[3]));
+            const double l = src[0], m = src[1];
+            const double r2 = l * l + m * m;
+            double* d = lmn + ((size_t)k * s_chunk + s) * 3;
+            d[0] = fc * l;
+            d[1] = fc * m;
+            d[2] = fc * (-r2 / (1.0 + sqrt(1.0 - r2)));  // sqrt(1 - l^2 - m^2) - 1, cancellation-free
         }
+        __syncthreads();
         for (int i = threadIdx.x; i < K * ns * N; i += blockDim.x) {
             const int p = i % N;
             const int ks = i / N;
             const int k = ks / ns, s = ks - k * ns;
-            const double* src = a.sky + ((size_t)k * a.S + s0 + s) * 4;
-            const double l = src[0], m = src[1];
-            const double r2 = l * l + m * m;
-            const double nm1 = -r2 / (1.0 + sqrt(1.0 - r2));  // sqrt(1 - l^2 - m^2) - 1, cancellation-free
-            const double turns = (f / C_LIGHT) * (uvw[p * 3 + 0] * l + uvw[p * 3 + 1] * m + uvw[p * 3 + 2] * nm1);
+            const double* d = lmn + ((size_t)k * s_chunk + s) * 3;
+            const double turns = uvw[p * 3 + 0] * d[0] + uvw[p * 3 + 1] * d[1] + uvw[p * 3 + 2] * d[2];
             const float fr = (float)(turns - rint(turns));
             float sn, cs;
             sincospif(2.0f * fr, &sn, &cs);
@@ -297,8 +304,9 @@ cudaError_t launch_extract_coh(const IngestArgs& a, float2* user_dst, cudaStream
 cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s) {
     const size_t budget = 96 * 1024;
     int s_chunk = a.S;
-    while (s_chunk > 1 && (size_t)a.K * s_chunk * (a.N * 8 + 4) > budget) s_chunk = (s_chunk + 1) / 2;
-    const size_t smem = (size_t)a.K * s_chunk * (a.N * 8 + 4);
+    // per source: its N station phasors (8 B each), its flux (4 B) and l, m, n - 1 (24 B)
+    while (s_chunk > 1 && (size_t)a.K * s_chunk * (a.N * 8 + 28) > budget) s_chunk = (s_chunk + 1) / 2;
+    const size_t smem = (size_t)a.K * s_chunk * (a.N * 8 + 28);
     dim3 grid(a.Tmax, a.A);
     k_predict<<<grid, 256, smem, s>>>(a, s_chunk);
     return cudaGetLastError();
