@@ -31,9 +31,9 @@
 namespace calib {
 namespace {
 
-// One stage = one whole diagonal. Ring depth: the Hessian pass (small stages, 4 CTAs per SM) keeps
-// two stages in flight; the trial pass (larger stages, shared memory for 3 CTAs per SM) one.
-template <bool HV> __host__ __device__ constexpr int nst() { return HV ? 3 : 2; }
+// One stage = one whole diagonal; one stage in flight while the other is computed (3 and 4 stages
+// measured no faster for the Hessian pass).
+template <bool HV> __host__ __device__ constexpr int nst() { return 2; }
 constexpr int BAR_BYTES = 64;  // barrier area, keeps what follows 16-byte aligned
 
 
