@@ -94,7 +94,8 @@ __device__ __forceinline__ long long cta_of_item(long long i, long long W, long 
 // pass's shared memory allows 3; the Hessian pass spends the registers on loads hoisted ahead of
 // their use); from K = 8 on, shared memory allows 2 CTAs (K = 8) or 1 (K >= 10) and the register
 // budget follows. Larger CTAs: 128 registers for the Hessian pass (2 CTAs of 256), unbounded for the trial.
-// Stage layout: [U: NP][K][2 rows] float4 (trial only) | [S: NP][KK] float2.
+// Stage layout: [U: n2][K][2 rows] float4 (trial only) | [S: n2][KK] float2, n2 = the diagonal's slot
+// count rounded up to even.
 template <int KB, bool HV, bool EXACT, bool SMALL>
 __global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB >= 8 ? 2 : 3)) : (HV ? 2 : 1))
     k_ss_sweep(const SSArgs a, const int stage_bytes) {
@@ -133,10 +134,10 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB
     auto issue = [&](int s2) {
         const size_t blk = ((size_t)iss_ag * D + iss_d) * NP;
         const int n = (2 * (iss_d + 1) == N) ? N / 2 : N;
-        const int n4 = (n + 3) & ~3;
+        const int n2 = (n + 1) & ~1;  // an even slot count keeps both copies multiples of 16 bytes
         if (++iss_d == D) { iss_d = 0; ++iss_ag; }
-        const uint32_t ub = HV ? 0u : (uint32_t)(n4 * K * 32);
-        const uint32_t sb = (uint32_t)(n4 * KK * 8);
+        const uint32_t ub = HV ? 0u : (uint32_t)(n2 * K * 32);
+        const uint32_t sb = (uint32_t)(n2 * KK * 8);
         unsigned char* buf = stage + (s2 % NST) * stage_bytes;
         uint64_t* b = &bar[s2 % NST];
         mbar_expect_tx(b, ub + sb);
@@ -228,10 +229,10 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB
             }
         }
         const int n = (2 * d == N) ? N / 2 : N;
-        const int n4 = (n + 3) & ~3;
+        const int n2 = (n + 1) & ~1;
         const unsigned char* buf = stage + (s % NST) * stage_bytes;
-        const float2* Us = reinterpret_cast<const float2*>(buf);  // [n4][K][2][2] (trial)
-        const float2* Ss = reinterpret_cast<const float2*>(buf + (HV ? 0 : n4 * K * 32)) + (size_t)g * KK;
+        const float2* Us = reinterpret_cast<const float2*>(buf);  // [n2][K][2][2] (trial)
+        const float2* Ss = reinterpret_cast<const float2*>(buf + (HV ? 0 : n2 * K * 32)) + (size_t)g * KK;
         const bool active = g < n;
         const int second = (g + d < N) ? g + d : g + d - N;
         // Row rr of X_k in column order (rr, 1 - rr): Hessian (S Q)_k; trial W'_k = U_k - (S P)_k - (S dP)_k.
@@ -388,9 +389,9 @@ cudaError_t prepare_ss_kernels() {
 }
 
 size_t ss_sweep_smem_bytes(int N, int K, bool hessvec, int* stage_bytes) {
-    const int KK = K * (K + 1) / 2, NP = (N + 3) / 4 * 4;
+    const int KK = K * (K + 1) / 2, N2 = (N + 1) / 2 * 2;  // slots copied per stage (even)
     const int per_slot = (hessvec ? 0 : K * 32) + KK * 8;
-    const int sb = ((NP * per_slot + 127) / 128) * 128;
+    const int sb = ((N2 * per_slot + 127) / 128) * 128;
     if (stage_bytes) *stage_bytes = sb;
     const int nstages = hessvec ? nst<true>() : nst<false>();
     return (size_t)nstages * sb + BAR_BYTES + (size_t)3 * K * N * 32 + 32 * 8;
