@@ -49,8 +49,6 @@ enum StatusBits : int { STATUS_TIMEOUT = 1, STATUS_NONFINITE = 2 };
 struct DiagDesc {     // one per (agent, diagonal)
     long long voff;   // float2 offset of the V block
     long long coff;   // float2 offset of the C block
-    long long uoff;   // float2 offset of the U block [n_pad][K][4] (sufficient statistics)
-    long long soff;   // float2 offset of the S block [n_pad][K(K+1)/2] (sufficient statistics)
     int slot_off;     // global index of the first slot of this diagonal in the slot arrays
     int n;            // active (unflagged) slots
     int n_pad;        // padded slot count (multiple of 4, >= n)

@@ -325,7 +325,7 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     c->desc_h.assign((size_t)A * D, DiagDesc{});
     c->slot_h.clear();
     c->slot_b_h.clear();
-    long long voff = 0, coff = 0, uoff = 0, soff = 0;
+    long long voff = 0, coff = 0;
     const int KK = K * (K + 1) / 2;
     int smax = 4;
     double alg_res = 0, alg_hv = 0, alg_ssh = 0, alg_sst = 0;
@@ -352,12 +352,8 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
             dd.n_pad = (n + 3) / 4 * 4;
             dd.voff = voff;
             dd.coff = coff;
-            dd.uoff = uoff;
-            dd.soff = soff;
             voff += (long long)c->T[a] * dd.n_pad * 4;
             coff += (long long)c->T[a] * dd.n_pad * K;
-            uoff += (long long)dd.n_pad * K * 4;
-            soff += (long long)dd.n_pad * KK;
             smax = std::max(smax, dd.n_pad);
             alg_res += (double)n * c->T[a] * (32.0 + 8.0 * K);
             alg_hv += (double)n * c->T[a] * (8.0 * K);
@@ -383,8 +379,6 @@ int build_layout(calib_ctx* c, const uint8_t* flags) {
     const long long NP = (N + 3) / 4 * 4;
     c->int_u = (long long)A * D * NP * K * 4;
     c->int_s = (long long)A * D * NP * KK;
-    (void)uoff;
-    (void)soff;
     c->slots_max = smax;
     c->alg_bytes[0] = alg_res;
     c->alg_bytes[1] = alg_hv;
