@@ -165,38 +165,41 @@ __global__ void __launch_bounds__(ZT) k_zupdate(const ConsArgs a) {
 
 // BZ_i = sum_l b_l(f_i) Z_l; Y_i += rho (J_i - BZ_i) (Eq. M3); per-agent ||J_ik - BZ_ik|| and
 // L_i(J_i, Z, Y_i) = g_i + Re tr(Y^H D) + rho/2 ||D||^2 with the new Y and BZ (Eq. sumtrace2).
-// One CTA per agent, one thread per (direction, station) block; the per-direction norms are summed
-// over the stations by one warp each (fixed order).
+// One CTA per agent, one thread per real entry of a (direction, station) block (independent
+// loads); a block's 8 entries sit in 8 aligned lanes and are summed by shuffles, the per-direction
+// norms over the stations by one warp each (fixed order).
 __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) {
     __shared__ double red[33];
     extern __shared__ double dds[];  // [K][N] ||J - BZ||^2 per block
     const int agent = blockIdx.x;
     const int iv = agent / a.P, f = agent - iv * a.P;
-    const int N = a.N, KN = a.K * N, M = a.M;
+    const int N = a.N, KN8 = a.K * N * 8, M = a.M;
     double bl[MAX_M];
 #pragma unroll
     for (int l = 0; l < MAX_M; ++l) bl[l] = l < M ? a.basis[f * M + l] : 0.0;
     double pen = 0.0;
-    for (int blk = threadIdx.x; blk < KN; blk += blockDim.x) {
-        const int k = blk / N, p = blk - k * N;
-        const double rk = a.rho[k];
-        const size_t o = ((size_t)agent * KN + blk) * 8;
-        const size_t zb = (((size_t)iv * a.K + k) * M * N + p) * 8;  // Z[iv][k][l][p][e] at l = 0
+    const int KN8r = (KN8 + blockDim.x - 1) / blockDim.x * blockDim.x;  // every lane runs every trip
+    for (int i = threadIdx.x; i < KN8r; i += blockDim.x) {
+        const bool on = i < KN8;  // KN8 is a multiple of 8: a block's 8 lanes are all on or all off
         double dd = 0.0;
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
+        if (on) {
+            const int k = i / (N * 8), pe = i - k * N * 8;  // pe = station * 8 + entry
+            const double rk = a.rho[k];
+            const size_t o = (size_t)agent * KN8 + i;
+            const double* z = a.Z + ((size_t)iv * a.K + k) * M * N * 8 + pe;  // Z[iv][k][l][p][e] at l = 0
             double bz = 0.0;
 #pragma unroll
             for (int l = 0; l < MAX_M; ++l)
-                if (l < M) bz = fma(bl[l], a.Z[zb + (size_t)l * N * 8 + e], bz);
-            const double d = (double)a.J[o + e] - bz;
-            const float ynew = update_y ? (float)((double)a.Y[o + e] + rk * d) : a.Y[o + e];
-            a.Y[o + e] = ynew;
-            a.BZ[o + e] = (float)bz;
-            dd = fma(d, d, dd);
+                if (l < M) bz = fma(bl[l], z[(size_t)l * N * 8], bz);
+            const double d = (double)a.J[o] - bz;
+            const float ynew = update_y ? (float)((double)a.Y[o] + rk * d) : a.Y[o];
+            a.Y[o] = ynew;
+            a.BZ[o] = (float)bz;
+            dd = d * d;
             pen += (double)ynew * d + 0.5 * rk * d * d;
         }
-        dds[blk] = dd;
+        for (int w = 4; w > 0; w >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, w);
+        if (on && (i & 7) == 0) dds[i >> 3] = dd;
     }
     pen = bsum(pen, red);  // its barriers also publish dds
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
