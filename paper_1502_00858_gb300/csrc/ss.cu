@@ -15,7 +15,7 @@
 // and there is no partial last wave. The statistics are in the full circulant layout (slot i of
 // diagonal d is the pair (i, (i+d) mod N), zero statistics where flagged), so thread pair g owns
 // station g as the first station of its slot in every diagonal: it keeps that station's rows of
-// J and eta (or x) and its first-station sums in registers for the whole agent, and only the
+// J and eta (or the trial point J') and its first-station sums in registers for the whole agent, and only the
 // second station (g+d) mod N goes through shared memory. A CTA stages J and eta of its current
 // agent, streams the per-slot statistics of one diagonal per stage through a cp.async.bulk ring
 // (mbarrier, bounded waits), and writes the station sums as one partial per (agent, piece) when
@@ -23,8 +23,9 @@
 // Two threads per slot, one per row of the 2x2 blocks: thread rr forms row rr of Q_l (or P_l and
 // dP_l), of the S-weighted sums X_k and of both station terms; the second station's term
 // X_k^H J_f needs column rr of X_k, whose other entry comes from the partner lane. Within a
-// diagonal every station is the second element of exactly one slot, so the shared-memory updates
-// of a diagonal are conflict-free (no atomics).
+// diagonal every station is the second element of at most one slot, so the shared-memory updates
+// of a diagonal are conflict-free (no atomics). The trial pass reads J' and forms the step as
+// x = J' - J (dP_l = x_pl J'_ql^H + J_pl x_ql^H, the same model change).
 #include "calib_internal.cuh"
 #include "tma.cuh"
 
