@@ -261,6 +261,17 @@ int calib_eval_noalloc(int n_agents, int n_stations, int n_baselines, int n_dirs
                        const void* Y, const void* BZ, const double* rho, double* L, double* g,
                        void* grad, void* cuda_stream);
 
+/* Self-test of the failure path shared by every kernel that waits on its own bulk copies: one
+ * CTA waits, with the library's bounded wait (about one second of SM clock), on an mbarrier
+ * phase. complete_phase != 0 completes the phase before the wait (control: returns CALIB_OK);
+ * complete_phase == 0 leaves it pending, so the wait gives up, the kernel records a timeout in
+ * a status word and returns, and the call returns CALIB_ETIMEOUT with the context of the device
+ * still usable. No copy is issued, so nothing is in flight when the wait gives up. The paper has
+ * no counterpart. cuda_stream as in calib_options (NULL = legacy default); the call allocates a
+ * 4-byte status word, synchronises the stream, and writes the kernel's duration in milliseconds
+ * (CUDA events) to elapsed_ms (may be NULL). CALIB_ECUDA if a CUDA call fails. */
+int calib_selftest_bounded_wait(int complete_phase, double* elapsed_ms, void* cuda_stream);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char* calib_last_error(void);
 

@@ -25,7 +25,7 @@ EXPORTED = [
     "calib_profile_read", "calib_launch_count", "calib_last_error", "calib_destroy", "calib_eval_noalloc",
     "calib_autotune", "calib_mlp_create", "calib_mlp_num_params", "calib_mlp_set_weights", "calib_mlp_get_weights",
     "calib_mlp_forward", "calib_mlp_grad", "calib_mlp_train_step", "calib_mlp_destroy", "calib_get_features",
-    "calib_warm_start",
+    "calib_warm_start", "calib_selftest_bounded_wait",
 ]
 
 
@@ -90,6 +90,7 @@ def load(path: str = LIB_PATH):
         "calib_mlp_destroy": (None, [vp]),
         "calib_get_features": (i, [vp, vp, i]),
         "calib_warm_start": (i, [vp, vp, vp, vp, vp, i]),
+        "calib_selftest_bounded_wait": (i, [i, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -256,6 +257,14 @@ def calib_profile_read(ctx):
 
 def calib_launch_count(ctx) -> int:
     return int(load().calib_launch_count(ctx))
+
+
+def calib_selftest_bounded_wait(complete_phase: bool, stream: int = 0) -> float:
+    """Runs the bounded-wait self-test; returns the kernel's duration in ms, raises CalibError
+    (code CALIB_ETIMEOUT) when the wait gave up."""
+    ms = C.c_double(0.0)
+    _check(load().calib_selftest_bounded_wait(int(bool(complete_phase)), C.byref(ms), C.c_void_p(stream)))
+    return ms.value
 
 
 def calib_destroy(ctx):

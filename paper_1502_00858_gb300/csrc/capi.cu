@@ -12,6 +12,26 @@
 
 #include "calib.h"
 #include "calib_internal.cuh"
+#include "tma.cuh"
+
+namespace calib {
+
+// One CTA waits, with the same bounded wait as the sweeps' copy ring, on an mbarrier phase that
+// completes only if complete_phase is set (one arrival on a count-1 barrier). No copy is issued, so
+// when the wait gives up nothing is in flight and the CTA can return at once.
+__global__ void k_wait_selftest(int complete_phase, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (complete_phase && threadIdx.x == 0) mbar_arrive(&bar);
+    const bool ok = mbar_wait_bounded(&bar, 0u);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, STATUS_TIMEOUT);
+}
+
+}  // namespace calib
 
 using namespace calib;
 
@@ -1297,6 +1317,34 @@ int calib_autotune(calib_ctx* c, int* split, int* split_trial, int cap, int* can
         if (ms_trial) ms_trial[i] = c->tune_log[i].tr;
     }
     if (n_cand) *n_cand = n;
+    return CALIB_OK;
+}
+
+int calib_selftest_bounded_wait(int complete_phase, double* elapsed_ms, void* cuda_stream) {
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    int* status = nullptr;
+    if (dalloc(&status, 1) != cudaSuccess) return fail(CALIB_ENOMEM, "status word");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int h = 0;
+    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 128, 0, st>>>(complete_phase != 0, status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(status);
+    if (e != cudaSuccess) return fail(CALIB_ECUDA, std::string("bounded-wait self-test: ") + cudaGetErrorString(e));
+    if (elapsed_ms) *elapsed_ms = ms;
+    if (h & STATUS_TIMEOUT) return fail(CALIB_ETIMEOUT, "bounded-wait self-test: the wait gave up");
     return CALIB_OK;
 }
 

@@ -88,3 +88,26 @@ def test_calls_out_of_order_and_bad_data_are_rejected_and_the_library_stays_usab
         assert hist["resid_norm"][-1] < hist["resid_norm"][0]
     finally:
         capi.calib_destroy(ctx)
+
+
+def test_bounded_wait_gives_up_reports_timeout_and_leaves_the_device_usable():
+    # control: the barrier phase completes, the wait returns at once
+    ms = capi.calib_selftest_bounded_wait(True)
+    assert ms < 50.0
+    # a phase nothing completes: the wait gives up after its budget (about one second of SM
+    # clock), the call reports CALIB_ETIMEOUT, and the device's context stays usable
+    with pytest.raises(CalibError) as err:
+        capi.calib_selftest_bounded_wait(False)
+    assert err.value.code == capi.CALIB_ETIMEOUT
+    assert "gave up" in str(err.value)
+    assert capi.calib_selftest_bounded_wait(True) < 50.0
+    prob = make_problem("tiny_n8_k1", P=3, seed=32)
+    ul = user_layout(prob)
+    ctx = capi.calib_init(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
+                          n_intervals=prob["I"], n_samples=int(prob["T"][0]))
+    try:
+        capi.calib_set_data(ctx, ul["vis"], ul["coh"])
+        hist = capi.calib_admm_iter(ctx, 2)
+        assert np.all(np.isfinite(hist["objective"]))
+    finally:
+        capi.calib_destroy(ctx)
