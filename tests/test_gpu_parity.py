@@ -72,6 +72,8 @@ CASES = {
     # 700 samples per interval: the statistics pass's per-(agent, diagonal) block exceeds what it
     # stages in shared memory and it reads global memory directly
     "n8_t700": lambda: make_problem("tiny_n8_k1", N=8, P=3, T=700, seed=23),
+    # more than 64 stations (a 96-thread Hessian sweep, 3 warps) and four directions
+    "n66_k4": lambda: make_problem("adjoint_n16_k3", N=66, K=4, P=4, I=1, T=2, flag_max=0.05, seed=24),
 }
 
 
@@ -162,7 +164,7 @@ def run_both(lib, prob, n_iter, n_lm=10, n_cg=4, form="statistics"):
 
 @pytest.mark.parametrize("form", sorted(FORMS))
 @pytest.mark.parametrize("case", ["tiny_n8_k1", "ragged_n13_k3", "n2_single_baseline", "n10_k10_flagged", "n9_k7",
-                                  "n8_t700"])
+                                  "n8_t700", "n66_k4"])
 def test_admm_history_matches_oracle(lib, case, form):
     prob = CASES[case]()
     n_iter = 10 if case == "tiny_n8_k1" else 4
