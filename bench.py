@@ -42,10 +42,8 @@ UNIT = "vis*dir*iter/s"
 
 # DRAM traffic per launch of each sweep kernel from one ncu capture; valid only for the kernel
 # source it was taken on (sha256 prefix of the kernel's .cu file), else reported as null.
-NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum, profiles/k_ss_sweep_lofar_n62_k5.md and
-    # profiles/k_ss_stats_lofar_n62_k5.md
-    ("stats_hessvec", "913dd5f1f359"): 82.6e6,
-    ("stats_trial", "913dd5f1f359"): 185.6e6,
+NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum of one full capture each (summaries in profiles/)
+    ("stats_hessvec", "146072fb36a2"): 82.55e6,
     ("stats_pass", "173cbb0337ff"): 596.2e6,
 }
 KERNEL_SOURCE = {"sweep_residual": "sweep.cu", "sweep_hessvec": "sweep.cu",

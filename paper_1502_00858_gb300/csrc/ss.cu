@@ -133,6 +133,7 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB
 
     // Thread 0 issues the stages in order; (iss_ag, iss_d) is the item of the next one.
     int iss_ag = ag0, iss_d = d0;
+    const uint64_t pol = tid == 0 ? l2_evict_first() : 0ull;
     auto issue = [&](int s2) {
         const size_t blk = ((size_t)iss_ag * D + iss_d) * NP;
         const int n = (2 * (iss_d + 1) == N) ? N / 2 : N;
@@ -143,8 +144,8 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB
         unsigned char* buf = stage + (s2 % NST) * stage_bytes;
         uint64_t* b = &bar[s2 % NST];
         mbar_expect_tx(b, ub + sb);
-        if (!HV) bulk_g2s(buf, a.U + blk * K * 4, ub, b);
-        bulk_g2s(buf + ub, a.S + blk * KK, sb, b);
+        if (!HV) bulk_g2s_stream(buf, a.U + blk * K * 4, ub, b, pol);
+        bulk_g2s_stream(buf + ub, a.S + blk * KK, sb, b, pol);
     };
     if (tid == 0)
         for (int s2 = 0; s2 < min(NST - 1, S); ++s2) issue(s2);
@@ -396,6 +397,7 @@ __global__ void __launch_bounds__(128, 2) k_ss_hessvec(const SSArgs a, const int
     __syncthreads();
 
     int iss_ag = ag0, iss_d = d0;
+    const uint64_t pol = tid == 0 ? l2_evict_first() : 0ull;
     auto issue = [&](int s2) {
         const size_t blk = ((size_t)iss_ag * D + iss_d) * NP;
         const int n = (2 * (iss_d + 1) == N) ? N / 2 : N;
@@ -404,7 +406,7 @@ __global__ void __launch_bounds__(128, 2) k_ss_hessvec(const SSArgs a, const int
         const uint32_t sb = (uint32_t)(n2 * KK * 8);
         uint64_t* b = &bar[s2 % NST];
         mbar_expect_tx(b, sb);
-        bulk_g2s(stage + (s2 % NST) * stage_bytes, a.S + blk * KK, sb, b);
+        bulk_g2s_stream(stage + (s2 % NST) * stage_bytes, a.S + blk * KK, sb, b, pol);
     };
     if (tid == 0)
         for (int s2 = 0; s2 < min(NST - 1, S); ++s2) issue(s2);
