@@ -84,6 +84,27 @@ def residual(J, V, C, pq):
     return V - model_vis(J, C, pq)
 
 
+def corrected_residual(J, V, C, pq, subtract=None, correct=None):
+    """Residual visibilities after calibration, optionally corrected (Section 2: the solutions
+    correct the data, and the residual is the data minus the predicted model).
+
+    R_pq = V_pq - sum_{k in subtract} J_pk C_pqk J_qk^H, with subtract a boolean mask [K]
+    (None: every direction). With correct = k0 the residual is then corrected by that
+    direction's solutions, R_pq <- J_pk0^{-1} R_pq J_qk0^{-H}. Reading of the paper's order:
+    correcting the data first and subtracting the corrected model gives the same matrix,
+    because the correction is linear.
+    """
+    K = J.shape[0]
+    sub = np.ones(K, dtype=bool) if subtract is None else np.asarray(subtract, dtype=bool)
+    R = V - model_vis(J[sub], C[:, :, sub], pq)
+    if correct is not None:
+        p, q = pq[:, 0], pq[:, 1]
+        left = np.linalg.inv(J[correct, p])           # [B,2,2]
+        right = herm(np.linalg.inv(J[correct, q]))    # [B,2,2]
+        R = np.einsum("bij,btjk,bkl->btil", left, R, right)
+    return R
+
+
 def data_cost(J, V, C, pq) -> float:
     """g(J) = sum_t sum_{p<q} ||V_pq - sum_k J_pk C_pqk J_qk^H||^2 (Eq. mltheta / Eq. sum3)."""
     return float(np.sum(np.abs(residual(J, V, C, pq)) ** 2))

@@ -419,3 +419,53 @@ def test_predict_agrees_with_the_generator_s_factorised_simulation():
     a = O.predict_coherencies(uvw, sky, f, 150e6, pq)
     b = simulate_coherencies(uvw, sky, f, pq)
     np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-9)
+
+
+# ------------------------------------------------------------------ residual and correction (Section 2)
+
+def test_residual_of_noise_free_data_at_the_true_solutions_is_zero():
+    """Subtracting every direction's model at the solutions that generated noise-free data
+    leaves nothing; a transposed or unconjugated station product, or a dropped direction,
+    leaves the model behind."""
+    a = small_agent(40, N=5, K=3, T=2, noise=False)
+    R = O.corrected_residual(a["Jt"], a["V"], a["C"], a["pq"])
+    assert np.abs(R).max() < 1e-12 * np.abs(a["V"]).max()
+    # the same with correction by any direction: J^-1 0 J^-H = 0
+    R = O.corrected_residual(a["Jt"], a["V"], a["C"], a["pq"], correct=2)
+    assert np.abs(R).max() < 1e-11 * np.abs(a["V"]).max()
+
+
+def test_correcting_one_direction_s_data_returns_its_coherency():
+    """K = 2, data of both directions, direction 1 subtracted, the rest corrected by
+    direction 0: J_p0^-1 (J_p0 c_0 J_q0^H) J_q0^-H = c_0 I_2 for every baseline and sample.
+    Subtracting the wrong direction, correcting by the wrong one, or applying the
+    inverse on the wrong side fails."""
+    a = small_agent(41, N=4, K=2, T=3, noise=False)
+    R = O.corrected_residual(a["Jt"], a["V"], a["C"], a["pq"], subtract=[False, True], correct=0)
+    ref = a["C"][:, :, 0, None, None] * np.eye(2)
+    np.testing.assert_allclose(R, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    wrong = O.corrected_residual(a["Jt"], a["V"], a["C"], a["pq"], subtract=[True, False], correct=0)
+    assert np.abs(wrong - ref).max() > 1e-3
+
+
+def test_residual_with_identity_solutions_is_coherency_subtraction():
+    """J = I: the model of direction k is c_k I_2, so the residual is V - sum_k c_k I_2 and the
+    correction changes nothing."""
+    a = small_agent(42, N=4, K=3, T=2)
+    Jid = np.broadcast_to(np.eye(2), a["Jt"].shape).astype(complex)
+    R = O.corrected_residual(Jid, a["V"], a["C"], a["pq"], subtract=[True, False, True], correct=1)
+    ref = a["V"] - (a["C"][:, :, 0] + a["C"][:, :, 2])[..., None, None] * np.eye(2)
+    np.testing.assert_allclose(R, ref, rtol=1e-13, atol=1e-13)
+
+
+def test_correction_by_unitary_solutions_keeps_the_norm():
+    """Unitary J: J^-1 = J^H, so the correction preserves each 2x2 block's Frobenius norm;
+    with nothing subtracted, the corrected data of a unitary gauge equal the data rotated back."""
+    a = small_agent(43, N=4, K=2, T=2)
+    rng = np.random.default_rng(44)
+    U = np.linalg.qr(cn(rng, 2, 4, 2, 2))[0]
+    R = O.corrected_residual(U, a["V"], a["C"], a["pq"], subtract=[False, False], correct=1)
+    np.testing.assert_allclose(np.linalg.norm(R, axis=(-2, -1)), np.linalg.norm(a["V"], axis=(-2, -1)), rtol=1e-12)
+    p, q = a["pq"][:, 0], a["pq"][:, 1]
+    back = np.einsum("bji,btjk,bkl->btil", U[1, p].conj(), a["V"], U[1, q])
+    np.testing.assert_allclose(R, back, rtol=1e-12, atol=1e-12)
