@@ -325,6 +325,26 @@ def run_ours(args, world, rank, local):
             "share_of_step": v["total_ms"] / 1e3 / dt if dt else None}
         for k, v in prof.items()}
 
+    # residual visibilities of every direction at the final solutions (Section 2), after the timed
+    # region: one HBM stream reading V and C and writing R once per visibility
+    out_d = torch.empty(int(vis_d.numel()), dtype=torch.float32, device=dev)
+    for _ in range(2):
+        capi.calib_residual(cal.ctx, out_d)
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r_reps = 5
+    r0.record(stream)
+    for _ in range(r_reps):
+        capi.calib_residual(cal.ctx, out_d)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    r_s = r0.elapsed_time(r1) / 1e3 / r_reps
+    r_bytes = per_iter_units / prob["K"] * (32 + 8 * prob["K"] + 32)
+    roofline["residual_kernel"] = {"kernel": "residual", "bound": "hbm", "achieved": r_bytes / r_s / 1e9,
+                                   "peak": hbm_peak, "unit": "GB/s", "frac": r_bytes / r_s / 1e9 / hbm_peak,
+                                   "avg_launch_us": r_s * 1e6, "algorithmic_bytes_per_launch": r_bytes,
+                                   "traffic": None}
+    del out_d
+
     # end to end through the public API with host buffers: H2D of the visibilities, uvw and sky,
     # prediction, cold start, 30 iterations, D2H of the solutions.
     vis_h = torch.from_numpy(ul["vis"].view(np.float32)).pin_memory()

@@ -113,7 +113,8 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
  *        will supply them;
  *  flags uint8 [A][B], 1 = exclude this baseline of this agent from g (host or device per
  *        ptr_kind), or NULL = nothing flagged. Flags are fixed at the first call.
- * Rejects non-finite visibilities (CALIB_ENUMERIC) when ptr_kind is 0. */
+ * Rejects non-finite visibilities or coherencies (CALIB_ENUMERIC) when ptr_kind is 0; the
+ * context then holds no data (and no coherencies, if coh was given) until a call succeeds. */
 int calib_set_data(calib_ctx* ctx, const void* vis, const void* coh, const uint8_t* flags, int ptr_kind);
 
 /* Predict the scalar coherencies of point-source clusters (Eq. coh) on the GPU.
@@ -228,6 +229,20 @@ int calib_get_features(calib_ctx* ctx, float* X, int ptr_kind);
  * agent J = J_prev + network(J_prev, B_f Z_prev, f) where that gives the lower L_i, else J = J_prev
  * (mlp NULL: always J_prev). chose [A] (may be NULL) receives 1 where the network's start was kept. */
 int calib_warm_start(calib_ctx* ctx, calib_mlp* mlp, const void* J_prev, const void* Z_prev, int* chose, int ptr_kind);
+
+/* Residual visibilities after calibration (Section 2: the solutions correct the data, and the
+ * residual is the data minus the predicted model), from the context's visibilities, coherencies and
+ * current solutions J (after calib_admm_iter, calib_set_initial or calib_warm_start):
+ *    R_pq = V_pq - sum_{k : subtract[k] != 0} J_pk C_pqk J_qk^H,
+ * then, if correct_dir >= 0, R_pq <- J_p,c^-1 R_pq J_q,c^-H with c = correct_dir (the data corrected
+ * for that direction's errors; correcting first and subtracting the corrected model is the same).
+ *  subtract: host int32 [K], nonzero = subtract direction k's model; NULL = every direction.
+ *  out: c64 [A][B][T_a][2][2], the layout of calib_set_data's visibilities; host (ptr_kind 0,
+ *       written before return) or device (ptr_kind 1, stream-ordered on the context's stream).
+ *       Flagged baselines are written as zeros. A singular J_p,c gives non-finite values there.
+ * Returns CALIB_ESTATE before visibilities and coherencies are set, CALIB_EINVAL for correct_dir
+ * outside [-1, K). */
+int calib_residual(calib_ctx* ctx, const int32_t* subtract, int correct_dir, void* out, int ptr_kind);
 
 /* Number of kernels this context has launched since creation (all kinds). */
 long long calib_launch_count(calib_ctx* ctx);

@@ -43,6 +43,12 @@ class Calibrator:
         out = np.zeros(int(self.B * self.T.sum() * self.K), dtype=np.complex64)
         return capi.calib_get_coherencies(self.ctx, out)
 
+    def residual(self, subtract=None, correct=None):
+        """V - the model of the subtracted directions (all by default), corrected by direction
+        `correct`'s solutions if given; visibility layout [A][B][T_a][2][2] flattened."""
+        out = np.zeros(int(self.B * self.T.sum() * 4), dtype=np.complex64)
+        return capi.calib_residual(self.ctx, out, subtract, -1 if correct is None else int(correct))
+
     def reset(self):
         capi.calib_reset(self.ctx)
 

@@ -25,7 +25,7 @@ EXPORTED = [
     "calib_profile_read", "calib_launch_count", "calib_last_error", "calib_destroy", "calib_eval_noalloc",
     "calib_autotune", "calib_mlp_create", "calib_mlp_num_params", "calib_mlp_set_weights", "calib_mlp_get_weights",
     "calib_mlp_forward", "calib_mlp_grad", "calib_mlp_train_step", "calib_mlp_destroy", "calib_get_features",
-    "calib_warm_start", "calib_selftest_bounded_wait",
+    "calib_warm_start", "calib_selftest_bounded_wait", "calib_residual",
 ]
 
 
@@ -91,6 +91,7 @@ def load(path: str = LIB_PATH):
         "calib_get_features": (i, [vp, vp, i]),
         "calib_warm_start": (i, [vp, vp, vp, vp, vp, i]),
         "calib_selftest_bounded_wait": (i, [i, vp, vp]),
+        "calib_residual": (i, [vp, vp, i, vp, i]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -177,6 +178,15 @@ def calib_predict(ctx, uvw_m, sky, f0_hz):
 def calib_get_coherencies(ctx, out):
     p, k, _ = _ptr(out)
     _check(load().calib_get_coherencies(ctx, p, k))
+    return out
+
+
+def calib_residual(ctx, out, subtract=None, correct: int = -1):
+    """Residual (optionally corrected) visibilities into out (user visibility layout)."""
+    sub = None if subtract is None else np.ascontiguousarray(np.asarray(subtract).astype(np.int32))
+    sp = None if sub is None else sub.ctypes.data
+    p, k, _ = _ptr(out)
+    _check(load().calib_residual(ctx, sp, int(correct), p, k))
     return out
 
 

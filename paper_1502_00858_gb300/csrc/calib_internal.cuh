@@ -148,6 +148,17 @@ struct IngestArgs {
 };
 cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t s);
 cudaError_t launch_extract_coh(const IngestArgs& a, float2* user_dst, cudaStream_t s);
+struct ResidualArgs {
+    const float2* V; const float2* C;  // internal layouts
+    const float* J;                    // [A][K][N][2][2] complex
+    float2* out;                       // user layout [A][B][T_a][2][2]
+    const long long* vis_off;          // [A] float2 offset of each agent's block in out
+    const DiagDesc* desc; const int* slot; const int* slot_b; const int* T;
+    int A, D, K, N;
+    unsigned mask;                     // bit k: subtract direction k's model
+    int correct;                       // direction whose solutions correct the residual, -1: none
+};
+cudaError_t launch_residual(const ResidualArgs& a, cudaStream_t s);
 struct PredictArgs {
     const double* uvw;      // [I][Tmax][N][3]
     const double* sky;      // [K][S][4]

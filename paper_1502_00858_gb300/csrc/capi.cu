@@ -924,7 +924,12 @@ int calib_set_data(calib_ctx* c, const void* vis, const void* coh, const uint8_t
     c->need_eval = true;
     if (ptr_kind == 0) {
         CK(cudaStreamSynchronize(c->stream));
-        return check_status(c);
+        const int rc_st = check_status(c);
+        if (rc_st != CALIB_OK) {  // rejected data are not usable: the caller must set them again
+            c->data_set = false;
+            if (coh) c->coh_set = false;
+        }
+        return rc_st;
     }
     return CALIB_OK;
 }
@@ -999,6 +1004,49 @@ int calib_get_coherencies(calib_ctx* c, void* coh, int ptr_kind) {
     c->launches += 1;
     if (ptr_kind == 0) {
         CK(cudaMemcpyAsync(coh, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    return CALIB_OK;
+}
+
+int calib_residual(calib_ctx* c, const int32_t* subtract, int correct_dir, void* out, int ptr_kind) {
+    if (!c || !out) return fail(CALIB_EINVAL, "ctx and out are required");
+    if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
+    if (correct_dir < -1 || correct_dir >= c->K) return fail(CALIB_EINVAL, "correct_dir must be -1 or in [0, K)");
+    if (!c->data_set || !c->coh_set) return fail(CALIB_ESTATE, "visibilities and coherencies must be set first");
+    unsigned mask = 0;
+    for (int k = 0; k < c->K; ++k)
+        if (!subtract || subtract[k]) mask |= 1u << k;
+    const size_t bytes = (size_t)c->user_v * sizeof(float2);
+    void* dst = out;
+    if (ptr_kind == 0) {
+        int rc = ensure_staging(c, bytes);
+        if (rc) return rc;
+        dst = c->staging;
+    }
+    // flagged baselines have no slot in the layout: zero them (every output when any is flagged)
+    if (std::any_of(c->flags_h.begin(), c->flags_h.end(), [](uint8_t f) { return f != 0; }))
+        CK(cudaMemsetAsync(dst, 0, bytes, c->stream));
+    ResidualArgs ra{};
+    ra.V = c->V;
+    ra.C = c->C;
+    ra.J = c->J;
+    ra.out = static_cast<float2*>(dst);
+    ra.vis_off = c->vis_off_d;
+    ra.desc = c->desc;
+    ra.slot = c->slot;
+    ra.slot_b = c->slot_b;
+    ra.T = c->T_d;
+    ra.A = c->A;
+    ra.D = c->D;
+    ra.K = c->K;
+    ra.N = c->N;
+    ra.mask = mask;
+    ra.correct = correct_dir;
+    CK(launch_residual(ra, c->stream));
+    c->launches += 1;
+    if (ptr_kind == 0) {
+        CK(cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
     }
     return CALIB_OK;

@@ -71,6 +71,96 @@ __global__ void k_extract_coh(const IngestArgs a, float2* out) {
     }
 }
 
+// Residual visibilities (Section 2: the solutions correct the data, and the residual is the data
+// minus the predicted model). In the layout's station order (i, j), where the data are V_ij and the
+// coherencies c_ij: R = V_ij - sum_{k in mask} c_ij,k J_ik J_jk^H, then, with a correction
+// direction k0, R <- J_i,k0^-1 R J_j,k0^-H. A pair held reversed is written back as R^H, which is
+// the user-order residual (and correction) of the same baseline. One CTA per (diagonal, agent), one
+// thread per slot looping over the samples; reads V and C once and writes each residual once.
+struct cf { float x, y; };
+__device__ __forceinline__ cf cmulf(cf a, cf b) { return cf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ cf cmulcf(cf a, cf b) { return cf{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }  // conj(a) b
+__device__ __forceinline__ cf caddf(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
+struct m22 { cf e[2][2]; };
+__device__ __forceinline__ m22 ld_m22(const float4* rows) {
+    const float4 r0 = __ldg(rows), r1 = __ldg(rows + 1);
+    return m22{{{cf{r0.x, r0.y}, cf{r0.z, r0.w}}, {cf{r1.x, r1.y}, cf{r1.z, r1.w}}}};
+}
+// A B
+__device__ __forceinline__ m22 mmul(const m22& A, const m22& B) {
+    m22 o;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) o.e[r][c] = caddf(cmulf(A.e[r][0], B.e[0][c]), cmulf(A.e[r][1], B.e[1][c]));
+    return o;
+}
+// A^-1 by the adjugate: [[a11, -a01], [-a10, a00]] / (a00 a11 - a01 a10)
+__device__ __forceinline__ m22 minv(const m22& A) {
+    const cf a = cmulf(A.e[0][0], A.e[1][1]), b = cmulf(A.e[0][1], A.e[1][0]);
+    const cf det{a.x - b.x, a.y - b.y};
+    const float s = 1.f / (det.x * det.x + det.y * det.y);
+    const cf id{det.x * s, -det.y * s};  // 1 / det
+    m22 o;
+    o.e[0][0] = cmulf(A.e[1][1], id);
+    o.e[1][1] = cmulf(A.e[0][0], id);
+    o.e[0][1] = cmulf(cf{-A.e[0][1].x, -A.e[0][1].y}, id);
+    o.e[1][0] = cmulf(cf{-A.e[1][0].x, -A.e[1][0].y}, id);
+    return o;
+}
+__device__ __forceinline__ m22 mherm(const m22& A) {
+    m22 o;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) o.e[r][c] = cf{A.e[c][r].x, -A.e[c][r].y};
+    return o;
+}
+
+__global__ void __launch_bounds__(64) k_residual(const ResidualArgs a) {
+    const int d = blockIdx.x, agent = blockIdx.y;
+    const DiagDesc dsc = a.desc[(size_t)agent * a.D + d];
+    const int Ta = a.T[agent], K = a.K, N = a.N;
+    const float4* J = reinterpret_cast<const float4*>(a.J) + (size_t)agent * K * N * 2;  // [K][N][2 rows]
+    const float4* V = reinterpret_cast<const float4*>(a.V + dsc.voff);                 // [T][n_pad][2 rows]
+    const float2* C = a.C + dsc.coff;                                                   // [T][n_pad][K]
+    float4* out = reinterpret_cast<float4*>(a.out + a.vis_off[agent]);                 // [B][T_a][2 rows]
+    for (int g = threadIdx.x; g < dsc.n; g += blockDim.x) {
+        const int sl = a.slot[dsc.slot_off + g];
+        const int i = sl & 0xff, j = (sl >> 8) & 0xff, rev = (sl >> 16) & 1;
+        const long long b = a.slot_b[dsc.slot_off + g];
+        m22 Li{}, Rj{};
+        if (a.correct >= 0) {
+            Li = minv(ld_m22(J + ((size_t)a.correct * N + i) * 2));
+            Rj = mherm(minv(ld_m22(J + ((size_t)a.correct * N + j) * 2)));
+        }
+        for (int t = 0; t < Ta; ++t) {
+            const size_t pos = (size_t)t * dsc.n_pad + g;
+            m22 R = ld_m22(V + pos * 2);
+            for (int k = 0; k < K; ++k) {
+                if (!((a.mask >> k) & 1u)) continue;
+                const float2 c2 = __ldg(C + pos * K + k);
+                const cf c{c2.x, c2.y};
+                const m22 Ji = ld_m22(J + ((size_t)k * N + i) * 2), Jj = ld_m22(J + ((size_t)k * N + j) * 2);
+#pragma unroll
+                for (int r = 0; r < 2; ++r)
+#pragma unroll
+                    for (int cc = 0; cc < 2; ++cc) {
+                        // (J_i J_j^H)[r][cc] = J_i[r][0] conj(J_j[cc][0]) + J_i[r][1] conj(J_j[cc][1])
+                        const cf m = caddf(cmulcf(Jj.e[cc][0], Ji.e[r][0]), cmulcf(Jj.e[cc][1], Ji.e[r][1]));
+                        const cf cm = cmulf(c, m);
+                        R.e[r][cc] = cf{R.e[r][cc].x - cm.x, R.e[r][cc].y - cm.y};
+                    }
+            }
+            if (a.correct >= 0) R = mmul(mmul(Li, R), Rj);
+            if (rev) R = mherm(R);
+            float4* o = out + ((size_t)b * Ta + t) * 2;
+            o[0] = make_float4(R.e[0][0].x, R.e[0][0].y, R.e[0][1].x, R.e[0][1].y);
+            o[1] = make_float4(R.e[1][0].x, R.e[1][0].y, R.e[1][1].x, R.e[1][1].y);
+        }
+    }
+}
+
 // One CTA per (sample, agent); source chunks sized to fit the phasor table in shared memory.
 __global__ void __launch_bounds__(256) k_predict(const PredictArgs a, int s_chunk) {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -299,6 +389,11 @@ cudaError_t launch_ingest(const IngestArgs& a, cudaStream_t s) {
 cudaError_t launch_extract_coh(const IngestArgs& a, float2* user_dst, cudaStream_t s) {
     dim3 grid(a.D, a.A);
     k_extract_coh<<<grid, 256, 0, s>>>(a, user_dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_residual(const ResidualArgs& a, cudaStream_t s) {
+    dim3 grid(a.D, a.A);
+    k_residual<<<grid, 64, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s) {

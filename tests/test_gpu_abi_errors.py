@@ -73,6 +73,16 @@ def test_calls_out_of_order_and_bad_data_are_rejected_and_the_library_stays_usab
         with pytest.raises(CalibError) as err:
             capi.calib_admm_iter(ctx, 0)
         assert err.value.code == EINVAL
+        out = np.zeros(A * B * 1 * 4, np.complex64)
+        with pytest.raises(CalibError) as err:  # no coherencies yet
+            capi.calib_residual(ctx, out)
+        assert err.value.code == ESTATE
+        capi.calib_set_data(ctx, np.zeros(A * B * 4, np.complex64), coh)
+        with pytest.raises(CalibError) as err:
+            capi.calib_residual(ctx, out, correct=1)  # K = 1
+        assert err.value.code == EINVAL
+        capi.calib_residual(ctx, out, correct=0)  # J = I, V = 0: R = -c I
+        np.testing.assert_array_equal(out.reshape(-1, 2, 2), np.broadcast_to(-np.eye(2, dtype=np.complex64), (A * B, 2, 2)))
     finally:
         capi.calib_destroy(ctx)
 
