@@ -334,8 +334,11 @@ def agent_data(prob: dict, a: int):
 
 
 def admm(prob: dict, n_iter: int, n_lm: int = 10, n_cg: int = 4, C_list=None, J0=None,
-         Z0=None, intervals=None) -> dict:
+         Z0=None, intervals=None, jupdate=None) -> dict:
     """C-ADMM (Eq. M1, M2, M3; steps D1-D3) for every solution interval independently.
+
+    jupdate, if given, replaces the LM J-update: a callable (J, V, C, pq, Y, BZ, rho) -> J,
+    e.g. the RTR or SAGE solvers of oracle/rtr.py (Section 3 uses RTR, step D1 uses SAGE).
 
     Initialisation: J = identity blocks (or J0), Z = Y = 0 (Section 3). A warm start may
     also pass Z0 [I][K,M,N,2,2]; the first-iteration gauge projection is only applied
@@ -369,7 +372,10 @@ def admm(prob: dict, n_iter: int, n_lm: int = 10, n_cg: int = 4, C_list=None, J0
         BZs = [bz(Z, basis[i]) for i in range(P)]
         rec = []
         for n in range(n_iter):
-            Js = [lm_jupdate(Js[i], *data[i], Ys[i], BZs[i], rho, n_lm, n_cg) for i in range(P)]
+            if jupdate is None:
+                Js = [lm_jupdate(Js[i], *data[i], Ys[i], BZs[i], rho, n_lm, n_cg) for i in range(P)]
+            else:
+                Js = [jupdate(Js[i], *data[i], Ys[i], BZs[i], rho) for i in range(P)]
             if n == 0 and Z0 is None:
                 Js = gauge_align(Js, P // 2)
             Zn = z_update(Js, Ys, basis, rho)
