@@ -63,6 +63,8 @@ class ProblemSpec:
     fmin: float = 115e6
     fmax: float = 185e6
     seed: int = 0
+    n_bg: int = 0            # weak background sources, not corrupted by any Jones matrix
+    bg_flux_max: float = 0.1  # their peak flux (Jy), flat spectrum
 
     @property
     def M(self) -> int:
@@ -92,6 +94,13 @@ SPECS: dict[str, ProblemSpec] = {
     "warm_n62_k5": ProblemSpec("warm_n62_k5", N=62, K=5, P=64, I=3, T=10, n_src=20,
                                sky_kind="clusters", basis_kind="bernstein", degree=3,
                                rho=10.0, snr=10.0, n_admm=30, jones_kind="smooth_deg3", seed=4),
+    # Simulation I (Section 4): one direction, 47 stations, 32 channels over 115-185 MHz, 20
+    # samples, Jones varying in time and frequency (G = 4), 300 weak uncorrupted background
+    # sources, noise power 10 % of the signal power; ordinary polynomial basis.
+    "sim1_n47_k1": ProblemSpec("sim1_n47_k1", N=47, K=1, P=32, I=1, T=20, n_src=1,
+                               sky_kind="clusters", basis_kind="poly", degree=1,
+                               rho=5.0, snr=10.0, n_admm=50, jones_kind="sim1_time", seed=5,
+                               n_bg=300),
     # adjoint check size: 16 stations, 3 directions, 8 frequencies, 2 samples.
     "adjoint_n16_k3": ProblemSpec("adjoint_n16_k3", N=16, K=3, P=8, I=1, T=2, n_src=5,
                                   sky_kind="clusters", basis_kind="bernstein", degree=3,
@@ -190,6 +199,28 @@ def make_jones(rng: np.random.Generator, spec: ProblemSpec, freqs: np.ndarray) -
     raise ValueError(spec.jones_kind)
 
 
+def make_jones_time(rng: np.random.Generator, spec: ProblemSpec, freqs: np.ndarray, Tmax: int) -> np.ndarray:
+    """Simulation I Jones matrices [I,P,Tmax,K,N,2,2] (Section 4): every element is the product of a
+    time factor sin(a1 t' + 2 pi b1) + i sin(a2 t' + 2 pi b2) and a frequency polynomial
+    sum_{l=1..4} (g_l + i d_l) ((f - f0)/f0)^(l-1), with a1, a2, b1, b2, g_l, d_l ~ U(0,1) drawn per
+    station, direction and element. t' is the sample's time in hours since the start of the
+    observation (10 s samples; solution interval iv starts at iv * T samples)."""
+    I, P, K, N = spec.I, spec.P, spec.K, spec.N
+    G = 4
+    a = rng.uniform(0, 1, (4, K, N, 2, 2))       # a1, a2, b1, b2
+    gd = rng.uniform(0, 1, (2, G, K, N, 2, 2))   # g_l, d_l
+    x = (freqs - F0_HZ) / F0_HZ
+    xs = np.stack([x ** l for l in range(G)], 0)  # [G,P]
+    freq = np.einsum("lknij,lf->fknij", gd[0] + 1j * gd[1], xs)  # [P,K,N,2,2]
+    out = np.empty((I, P, Tmax, K, N, 2, 2), dtype=complex)
+    for iv in range(I):
+        tp = (iv * Tmax + np.arange(Tmax)) * SAMPLE_SECONDS / 3600.0  # hours
+        tm = (np.sin(a[0][None] * tp[:, None, None, None, None] + 2 * math.pi * a[2][None])
+              + 1j * np.sin(a[1][None] * tp[:, None, None, None, None] + 2 * math.pi * a[3][None]))  # [T,K,N,2,2]
+        out[iv] = freq[:, None] * tm[None]
+    return out
+
+
 # ----------------------------------------------------------------------------- forward simulation
 
 def simulate_coherencies(uvw_t: np.ndarray, sky: np.ndarray, f: float, pq: np.ndarray) -> np.ndarray:
@@ -258,12 +289,24 @@ def make_problem(spec: ProblemSpec | str, seed: int | None = None, *, I: int | N
     xyz = station_layout(rng, N)
     uvw = station_uvw(xyz, I, Tmax)
     sky = make_sky(rng, spec)
-    J_true = make_jones(rng, spec, freqs).reshape(A, K, N, 2, 2)
+    J_true_t = None
+    if spec.jones_kind == "sim1_time":
+        J_true_t = make_jones_time(rng, spec, freqs, Tmax).reshape(A, Tmax, K, N, 2, 2)
+        J_true = np.stack([J_true_t[a, :int(T_agent[a])].mean(axis=0) for a in range(A)])
+    else:
+        J_true = make_jones(rng, spec, freqs).reshape(A, K, N, 2, 2)
 
     flags = np.zeros((A, B), dtype=np.uint8)
     if spec.flag_max > 0:
         frac = rng.uniform(0.0, spec.flag_max, A)
         flags = (rng.uniform(0, 1, (A, B)) < frac[:, None]).astype(np.uint8)
+    sky_bg = None
+    if spec.n_bg > 0:  # weak background sources over the 7 x 7 degree field, flat spectrum
+        half = math.radians(3.5)
+        sky_bg = np.zeros((1, spec.n_bg, 4))
+        sky_bg[0, :, 0] = np.sin(rng.uniform(-half, half, spec.n_bg))
+        sky_bg[0, :, 1] = np.sin(rng.uniform(-half, half, spec.n_bg))
+        sky_bg[0, :, 2] = rng.uniform(0.0, spec.bg_flux_max, spec.n_bg)
 
     Cs, Vs = [], []
     sig, cnt = 0.0, 0
@@ -271,7 +314,13 @@ def make_problem(spec: ProblemSpec | str, seed: int | None = None, *, I: int | N
         iv, fi = divmod(a, P)
         Ta = int(T_agent[a])
         C = simulate_coherencies(uvw[iv, :Ta], sky, float(freqs[fi]), pq)
-        V = simulate_visibilities(J_true[a], C, pq)
+        if J_true_t is None:
+            V = simulate_visibilities(J_true[a], C, pq)
+        else:  # Jones matrices of every sample
+            V = np.concatenate([simulate_visibilities(J_true_t[a, t], C[:, t:t + 1], pq) for t in range(Ta)], axis=1)
+        if sky_bg is not None:  # uncorrupted: c_bg I_2
+            cb = simulate_coherencies(uvw[iv, :Ta], sky_bg, float(freqs[fi]), pq)[:, :, 0]
+            V = V + cb[:, :, None, None] * np.eye(2)
         sig += float(np.sum(np.abs(V[flags[a] == 0]) ** 2))
         cnt += int(np.sum(flags[a] == 0)) * Ta * 4
         Cs.append(C.astype(dtype, copy=False))
@@ -283,9 +332,14 @@ def make_problem(spec: ProblemSpec | str, seed: int | None = None, *, I: int | N
         for a in range(A):
             shape = Vs[a].shape
             Vs[a] = Vs[a] + (sigma * (rng.standard_normal(shape) + 1j * rng.standard_normal(shape))).astype(dtype, copy=False)
-    return dict(spec=spec, N=N, K=K, P=P, I=I, M=spec.M, B=B, A=A, pq=pq, freqs=freqs, basis=basis,
-                rho=rho, T=T_agent, flags=flags, uvw=uvw, sky=sky, f0=F0_HZ, J_true=J_true,
-                V=Vs, C=Cs, sigma=sigma, n_admm=spec.n_admm)
+    out = dict(spec=spec, N=N, K=K, P=P, I=I, M=spec.M, B=B, A=A, pq=pq, freqs=freqs, basis=basis,
+               rho=rho, T=T_agent, flags=flags, uvw=uvw, sky=sky, f0=F0_HZ, J_true=J_true,
+               V=Vs, C=Cs, sigma=sigma, n_admm=spec.n_admm)
+    if J_true_t is not None:
+        out["J_true_t"] = J_true_t  # [A,Tmax,K,N,2,2]; J_true is its mean over each agent's samples
+    if sky_bg is not None:
+        out["sky_bg"] = sky_bg
+    return out
 
 
 def agent_slices(T: np.ndarray, B: int) -> np.ndarray:
