@@ -46,6 +46,8 @@ class Calibrator:
     def residual(self, subtract=None, correct=None):
         """V - the model of the subtracted directions (all by default), corrected by direction
         `correct`'s solutions if given; visibility layout [A][B][T_a][2][2] flattened."""
+        if subtract is not None and np.asarray(subtract).shape != (self.K,):
+            raise ValueError(f"subtract must have one entry per direction ({self.K})")
         out = np.zeros(int(self.B * self.T.sum() * 4), dtype=np.complex64)
         return capi.calib_residual(self.ctx, out, subtract, -1 if correct is None else int(correct))
 
