@@ -1,11 +1,17 @@
-"""Simulation I (Section 4) through the float64 oracle at reduced size: the qualitative behaviour the
-section reports, checked on the oracle's C-ADMM with the Simulation I problem generator. Reduced
-problem: 10 stations, 8 channels, 20 samples, 20 C-ADMM iterations of 10 LM steps; normal
-calibration is each channel alone (rho 1e-6) with 30 LM steps. Three claims hold at this size: the
-lowest error is at rho = 50 for both F, the dual residual is lower for F = 2 than for F = 5, and F = 5
-has the higher error at the edge channels. The primal-residual ordering and distributed-beats-normal
-at every rho need more stations and iterations, and are left to the full-size run on the GPU."""
+"""Simulation I (Section 4) through the float64 oracle: the qualitative behaviour the section
+reports, checked on the oracle's C-ADMM with the Simulation I problem generator; normal calibration
+is each channel alone (rho 1e-6) with 30 LM steps, distributed calibration 10 LM steps per C-ADMM
+iteration.
+
+Default size (seconds): 10 stations, 8 channels, 20 iterations. Three claims hold there: the lowest
+error is at rho = 50 for both F, the dual residual is lower for F = 2 than for F = 5, and F = 5 has
+the higher error at the edge channels; rho = 50 also beats normal calibration. The primal-residual
+ordering and distributed-beats-normal at every rho need the paper's size: with
+SIM1_ORACLE_SIZE=47,32,50 (47 stations, 32 channels, 50 iterations; about 24 minutes on one core)
+the test asserts all five claims."""
 from __future__ import annotations
+
+import os
 
 import numpy as np
 import pytest
@@ -15,9 +21,13 @@ from paper_1502_00858_gb300 import sim1
 from synth import make_problem
 
 
+SIZE = tuple(int(v) for v in os.environ.get("SIM1_ORACLE_SIZE", "10,8,20").split(","))
+FULL = SIZE == (47, 32, 50)
+
+
 @pytest.fixture(scope="module")
 def results():
-    N, P, n_iter = 10, 8, 20
+    N, P, n_iter = SIZE
     prob = make_problem("sim1_n47_k1", N=N, P=P, seed=5)
     Jt = prob["J_true_t"][:, :, 0]
     zero = np.zeros((1, N, 2, 2), complex)
@@ -46,3 +56,5 @@ def test_simulation_one_behaviour_on_the_oracle(results):
     normal = float(np.mean(results["normal"]["error"]))
     for F in sim1.F_VALUES:
         assert float(np.mean(results[f"F{F}_rho50"]["error"])) < normal
+    if FULL:
+        assert all(claims.values()), claims
