@@ -241,6 +241,8 @@ def run_ours(args, world, rank, local):
         cal.hessvec(J, J)
         capi.calib_reset(cal.ctx)
         capi.calib_admm_iter(cal.ctx, 1, want_hist=False)
+        out_d = torch.empty(int(vis_d.numel()), dtype=torch.float32, device=dev)
+        capi.calib_residual(cal.ctx, out_d)
         torch.cuda.synchronize()
         cal.close()
         print("kernels-only run done", flush=True)

@@ -24,8 +24,10 @@ the adopted reading is stated at the function:
 
 Parity status: all functions are pinned by tests in tests/test_oracle_pins.py
 (finite differences, closed forms, least-squares brute force, invariants and
-hand-derived values) except the physical-accuracy claims of the paper's figures,
-which print no numbers.
+hand-derived values) and tests/test_oracle_schedule_pins.py (the LM damping
+schedule over several steps against an independent dense LM, and the Section 4
+records of admm worked out by hand), except the physical-accuracy claims of the
+paper's figures, which print no numbers.
 
 Shapes (per agent, complex128): J, Y, BZ [K,N,2,2]; V [B,T,2,2]; C [B,T,K] with the
 coherency matrix c * I_2 (Eq. coh); pq int [B,2] with p<q.
@@ -229,7 +231,7 @@ def pcg(J, C, pq, grad, G, rho, mu, n_cg):
 LM_TAU = 1e-3
 
 
-def lm_jupdate(J0, V, C, pq, Y, BZ, rho, n_lm, n_cg, stats=None):
+def lm_jupdate(J0, V, C, pq, Y, BZ, rho, n_lm, n_cg, stats=None, trace=None):
     """Minimise L_i(J, Z^n, Y^n) over J (Eq. M1) by n_lm Levenberg-Marquardt steps.
 
     Each step: PCG solve of the damped GN system, predicted decrease from the
@@ -237,6 +239,9 @@ def lm_jupdate(J0, V, C, pq, Y, BZ, rho, n_lm, n_cg, stats=None):
     (L(J) - L(J+x)) / pred, accept when pred > 0 and L(J+x) < L(J) (finite),
     Nielsen damping update mu *= max(1/3, 1-(2 ratio-1)^3) on accept, mu *= nu,
     nu *= 2 on reject. mu0 = 1e-3 * max_{p,k} max diag(G_pk + rho_k/2 I).
+    trace, if a list, receives one record per step (recording only): the damping
+    (mu, nu) the step was solved with, L at the current point and at the trial
+    point, pred, and whether the step was accepted.
     """
     J = J0.copy()
     L = aug_lagrangian(J, V, C, pq, Y, BZ, rho)
@@ -251,6 +256,9 @@ def lm_jupdate(J0, V, C, pq, Y, BZ, rho, n_lm, n_cg, stats=None):
         pred = -(h_inner(x, grad) + 0.5 * h_inner(x, hess_lagrangian(J, x, C, pq, rho)))
         Jt = J + x
         Lt = aug_lagrangian(Jt, V, C, pq, Y, BZ, rho)
+        if trace is not None:
+            trace.append(dict(mu=mu, nu=nu, L=L, Lt=Lt, pred=pred,
+                              accepted=bool(pred > 0.0 and math.isfinite(Lt) and Lt < L)))
         if pred > 0.0 and math.isfinite(Lt) and Lt < L:
             ratio = (L - Lt) / pred
             J, L = Jt, Lt
