@@ -250,14 +250,16 @@ long long calib_launch_count(calib_ctx* ctx);
 /* Size in bytes of the fixed device array that calib_eval_noalloc uses as scratch. */
 #define CALIB_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
 
-/* calib_eval without any allocation, for callers that cannot call cudaMalloc: work enqueued
- * while a global-mode CUDA stream capture is active (cudaMalloc is not permitted there),
- * applications whose device memory is all reserved by their own pool allocator, and
- * latency-critical pipelines that cannot take the implicit device synchronisation of
- * cudaMalloc / cudaFree. The paper has no counterpart; it is a deployment variant of the
- * residual/gradient evaluation.
+/* calib_eval without any allocation, for callers that cannot call cudaMalloc: applications
+ * whose device memory is all reserved by their own pool allocator (a cudaMalloc would fail or
+ * fragment it), and latency-critical pipelines that cannot take the implicit device
+ * synchronisation of cudaMalloc / cudaFree. The paper has no counterpart; it is a deployment
+ * variant of the residual/gradient evaluation.
  *  Inputs (device pointers, read in order on cuda_stream; NULL stream = legacy default):
- *    pq int32 [B][2] with p<q; vis c64 [A][B][T][2][2]; coh c64 [A][B][T][K];
+ *    pq int32 [B][2] with 0 <= p < q < N, checked on the device: a pair outside that range is
+ *       skipped and every agent's L, g and grad are written as NaN (the call itself returns
+ *       CALIB_OK, since it does not wait for the GPU);
+ *    vis c64 [A][B][T][2][2]; coh c64 [A][B][T][K];
  *    J c64 [A][K][N][2][2]; Y and BZ c64 [A][K][N][2][2] (either NULL = zero); rho host float64 [K].
  *    Every agent uses all B baselines and T samples (no flags).
  *  Outputs (device): L and g float64 [A] (either NULL = not written), grad c64 [A][K][N][2][2]
@@ -268,9 +270,11 @@ long long calib_launch_count(calib_ctx* ctx);
  * device looks up the array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture. All calls share the array and it keeps the
  * last call's contents (each call rewrites what it reads, so nothing needs clearing); calls that
- * overlap on the GPU race on it and must be serialised by the caller. Returns after enqueueing
- * (asynchronous); errors of the launch are reported, errors of execution surface at the next
- * synchronisation. */
+ * overlap on the GPU race on it and must be serialised by the caller. The station sums are
+ * accumulated with shared-memory atomics in no fixed order, so, unlike calib_eval, results are
+ * not bitwise reproducible from call to call (they agree to float32 rounding). Returns after
+ * enqueueing (asynchronous); errors of the launch are reported, errors of execution surface at
+ * the next synchronisation. */
 int calib_eval_noalloc(int n_agents, int n_stations, int n_baselines, int n_dirs, int n_samples,
                        const int32_t* pq, const void* vis, const void* coh, const void* J,
                        const void* Y, const void* BZ, const double* rho, double* L, double* g,

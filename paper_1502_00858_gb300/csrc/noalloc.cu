@@ -2,14 +2,17 @@
 // allocate device memory. It takes every input and output from the caller and keeps its only
 // scratch - per-chunk partial station sums - in a fixed array in this file's device memory.
 //
-// Who needs it: code that enqueues work while a CUDA stream capture in global mode is active
-// (cudaMalloc is not permitted there), applications whose device memory is entirely reserved
-// by their own pool allocator, and latency-critical pipelines that cannot afford the implicit
-// device synchronisation of cudaMalloc / cudaFree.
+// Who needs it: applications whose device memory is entirely reserved by their own pool
+// allocator (a cudaMalloc would fail or fragment that pool), and latency-critical pipelines that
+// cannot afford the implicit device synchronisation of cudaMalloc / cudaFree.
 //
 // Scratch rules: the array is shared by every call in the process on a given device and keeps
 // the previous call's contents; each call overwrites every slot it later reads, so nothing needs
 // clearing. Calls that overlap on the GPU (different streams, or other threads) race on it.
+// The station sums are accumulated with shared-memory atomics, so the result is not bitwise
+// reproducible from call to call (it varies in the last bits; calib_eval is reproducible).
+// Station pairs are validated on the device: a pair outside 0 <= p < q < N is skipped, and its
+// chunk marks the agent's results invalid (L, g and grad are written as NaN).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -67,12 +70,22 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc_sweep(const NoAllocArgs 
     }
     __syncthreads();
     double cost = 0.0;
+    bool bad = false;  // this thread met a station pair outside 0 <= p < q < N
     const int b_begin = chunk * NA_BASELINES_PER_CTA;
     const int b_end = min(a.B, b_begin + NA_BASELINES_PER_CTA);
     for (int b0 = b_begin; b0 < b_end; b0 += NA_THREADS / 4) {
         const int b = b0 + (tid >> 2);
-        const bool active = b < b_end;
-        const int p = active ? a.pq[2 * b] : 0, q = active ? a.pq[2 * b + 1] : 0;
+        int p = 0, q = 0;
+        bool active = b < b_end;
+        if (active) {
+            p = a.pq[2 * b];
+            q = a.pq[2 * b + 1];
+            if (!(p >= 0 && p < q && q < N)) {  // never index shared memory with a bad pair
+                bad = true;
+                active = false;
+                p = q = 0;
+            }
+        }
         float2 P[16], W[16];
         for (int k = 0; k < K; ++k) {
             const float2* jp = Js + (k * N + p) * 4;
@@ -113,13 +126,15 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc_sweep(const NoAllocArgs 
     __syncthreads();
     float2* out = reinterpret_cast<float2*>(a.part) + ((size_t)agent * a.n_chunks + chunk) * KN4;
     for (int i = tid; i < KN4; i += blockDim.x) out[i] = acc[i];
+    const bool any_bad = __syncthreads_or(bad);
     for (int o = 16; o > 0; o >>= 1) cost += __shfl_down_sync(0xffffffffu, cost, o);
     if (lane == 0) red[tid >> 5] = cost;
     __syncthreads();
     if (tid == 0) {
         double s = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-        a.part_cost[(size_t)agent * a.n_chunks + chunk] = s;
+        // a NaN cost is the chunk's "invalid pair" mark (read by k_noalloc_finish)
+        a.part_cost[(size_t)agent * a.n_chunks + chunk] = any_bad ? __longlong_as_double(0x7ff8000000000000LL) : s;
     }
 }
 
@@ -129,6 +144,9 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc_finish(const NoAllocArgs
     __shared__ double red[33];
     const int agent = blockIdx.x;
     const int KN8 = a.K * a.N * 8;
+    bool bad = false;  // a chunk of this agent met an invalid station pair
+    for (int ch = 0; ch < a.n_chunks; ++ch) bad = bad || isnan(a.part_cost[(size_t)agent * a.n_chunks + ch]);
+    const float fnan = __int_as_float(0x7fc00000);
     double pen = 0.0;
     for (int i = threadIdx.x; i < KN8; i += blockDim.x) {
         const size_t o = (size_t)agent * KN8 + i;
@@ -137,7 +155,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc_finish(const NoAllocArgs
         for (int ch = 0; ch < a.n_chunks; ++ch) s += a.part[((size_t)agent * a.n_chunks + ch) * KN8 + i];
         const double y = a.Y ? (double)a.Y[o] : 0.0;
         const double d = (double)a.J[o] - (a.BZ ? (double)a.BZ[o] : 0.0);
-        a.grad[o] = (float)((double)s + 0.5 * y + 0.5 * rk * d);
+        a.grad[o] = bad ? fnan : (float)((double)s + 0.5 * y + 0.5 * rk * d);
         pen += y * d + 0.5 * rk * d * d;
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -148,6 +166,7 @@ __global__ void __launch_bounds__(NA_THREADS) k_noalloc_finish(const NoAllocArgs
         double p = 0.0, g = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) p += red[i];
         for (int ch = 0; ch < a.n_chunks; ++ch) g += a.part_cost[(size_t)agent * a.n_chunks + ch];
+        if (bad) g = p = __longlong_as_double(0x7ff8000000000000LL);
         if (a.g) a.g[agent] = g;
         if (a.L) a.L[agent] = g + p;
     }
