@@ -9,7 +9,10 @@ Metric: visibilities x directions x ADMM iterations per second.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 Under torchrun each rank calibrates its own batch (seed offset by rank): no data-path
-collective, weak scaling. --impl reference times the FP64 CPU oracle on a bounded sample.
+collective, weak scaling. --impl reference times the FP64 CPU oracle on a bounded sample,
+spread over every host core (one process per core, each calibrating its own subband group).
+The default run also measures the batched uneven workload (256 subbands x 10 intervals, K=10,
+5/10/20 samples, flagged baselines, 50 iterations) and reports it as the nested "uneven" field.
 """
 from __future__ import annotations
 
@@ -44,25 +47,30 @@ UNIT = "vis*dir*iter/s"
 # source it was taken on (sha256 prefix of the kernel's .cu file), else reported as null.
 NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum of one full capture each (summaries in profiles/)
     ("stats_hessvec", "146072fb36a2"): 82.55e6,
-    ("stats_pass", "173cbb0337ff"): 596.2e6,
+    ("stats_pass", "532c6d147726"): 595.5e6,
+    ("residual", "532c6d147726"): 615.2e6,
 }
 KERNEL_SOURCE = {"sweep_residual": "sweep.cu", "sweep_hessvec": "sweep.cu",
-                 "stats_hessvec": "ss.cu", "stats_trial": "ss.cu", "stats_pass": "data.cu"}
+                 "stats_hessvec": "ss.cu", "stats_trial": "ss.cu", "stats_pass": "data.cu", "residual": "data.cu"}
 # The sufficient-statistics passes do 13-17 real flops per algorithmic byte at K=5, above the FP32
 # ridge (~12 flop/B): their roofline is the FP32 pipe. The direct passes are below it (HBM).
 ALU_BOUND = {"stats_hessvec", "stats_trial"}
-SMS, FP32_LANES_PER_SM = 152, 128
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per Blackwell SM (4 sub-partitions x 32)
 
 
-def peaks():
-    """(HBM GB/s, FP32 TFLOP/s, source). FP32 peak = SMs x FP32 lanes x 2 flops (FMA) x max SM clock."""
+def peaks(sms: int):
+    """(HBM GB/s, FP32 TFLOP/s, how the FP32 peak was derived). FP32 peak = SMs (read from the
+    device) x FP32 lanes per SM x 2 flops (FMA) x the maximum SM clock measured on the box."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
             mp = json.load(fh)
-        mhz = float(mp.get("sm_max_mhz", 2070.0))
-        return float(mp["hbm_gbs"]), SMS * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, "measured"
+        mhz, hbm, kind = float(mp.get("sm_max_mhz", 2070.0)), float(mp["hbm_gbs"]), "measured"
     except Exception:
-        return 6800.0, SMS * FP32_LANES_PER_SM * 2 * 2070e6 / 1e12, "fallback"
+        mhz, hbm, kind = 2070.0, 6800.0, "fallback"
+    fp32 = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    how = (f"FP32: {sms} SMs (device attribute) x {FP32_LANES_PER_SM} lanes x 2 flops x {mhz:.0f} MHz "
+           f"({kind} max SM clock) = {fp32:.1f} TFLOP/s; HBM: {hbm:.1f} GB/s ({kind} copy bandwidth)")
+    return hbm, fp32, how
 
 
 def source_hash(kind: str) -> str:
@@ -152,23 +160,81 @@ def units(prob) -> float:
 
 # ----------------------------------------------------------------------------- CPU oracle legs
 
-def oracle_sample(prob, n_freq: int):
-    """One C-ADMM iteration of the FP64 oracle on interval 0 restricted to its first n_freq
-    subbands (same per-agent data, same LM/PCG schedule). Returns (seconds, vis*dir*iter)."""
+ORACLE_FREQS = 4  # subbands per oracle task: one C-ADMM problem of 4 agents
+
+
+def oracle_task(sub: dict) -> tuple[float, float]:
+    """One C-ADMM iteration of the FP64 oracle on one task (runs in a worker process).
+    Returns (seconds, vis*dir*iter)."""
     from oracle import admm as O
 
-    up = (lambda xs: [np.asarray(x, dtype=np.complex128) for x in xs]) if isinstance(prob["V"], list) else \
-        (lambda xs: np.asarray(xs, dtype=np.complex128))
-    sub = dict(prob, P=n_freq, I=1, A=n_freq, basis=prob["basis"][:n_freq], freqs=prob["freqs"][:n_freq],
-               V=up(prob["V"][:n_freq]), C=up(prob["C"][:n_freq]), flags=prob["flags"][:n_freq], T=prob["T"][:n_freq])
     t0 = time.perf_counter()
     O.admm(sub, 1, n_lm=N_LM, n_cg=N_CG)
-    dt = time.perf_counter() - t0
-    return dt, units(sub)
+    return time.perf_counter() - t0, units(sub)
 
 
-def cpu_threads() -> int:
-    return 1  # NumPy einsum/matmul on 2x2 blocks runs single-threaded; BLAS pinned to one thread below
+def oracle_tasks(prob, n_tasks: int, n_freq: int = ORACLE_FREQS) -> list[dict]:
+    """n_tasks sub-problems of the workload: interval iv, subbands [g n_freq, (g+1) n_freq), over
+    (iv, g) in order, each a C-ADMM problem with the same per-agent data and LM/PCG schedule."""
+    tasks = []
+    for iv in range(prob["I"]):
+        for g in range(prob["P"] // n_freq):
+            if len(tasks) == n_tasks:
+                return tasks
+            ag = [iv * prob["P"] + g * n_freq + f for f in range(n_freq)]
+            fr = slice(g * n_freq, (g + 1) * n_freq)
+            tasks.append(dict(N=prob["N"], K=prob["K"], P=n_freq, M=prob["M"], I=1, A=n_freq, pq=prob["pq"],
+                              rho=prob["rho"], basis=prob["basis"][fr], freqs=prob["freqs"][fr],
+                              V=[np.asarray(prob["V"][a], dtype=np.complex128) for a in ag],
+                              C=[np.asarray(prob["C"][a], dtype=np.complex128) for a in ag],
+                              flags=prob["flags"][ag], T=prob["T"][ag]))
+    return tasks
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model")):
+                    return line.split(":", 1)[1].strip()
+        import platform
+        return platform.processor() or platform.machine()
+    except Exception:
+        return "unknown"
+
+
+class OraclePool:
+    """The float64 oracle on every host core: a spawn-started process pool (one worker per core,
+    BLAS at one thread each), each worker calibrating its own subband group."""
+
+    def __init__(self, workers: int):
+        import multiprocessing as mp
+
+        self.workers = workers
+        self.pool = mp.get_context("spawn").Pool(workers)
+
+    def run(self, tasks) -> tuple[float, float]:
+        """Wall seconds and total vis*dir*iter of the tasks, one per worker."""
+        t0 = time.perf_counter()
+        res = self.pool.map(oracle_task, tasks, chunksize=1)
+        return time.perf_counter() - t0, float(sum(u for _, u in res))
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def oracle_sample_text(workers: int, n_tasks: int, P: int, seconds: float) -> str:
+    return (f"one C-ADMM iteration (10 LM x 4 PCG) of {n_tasks} tasks run concurrently on {workers} processes, "
+            f"each task one solution interval restricted to {ORACLE_FREQS} of its {P} subbands "
+            f"({seconds:.1f} s wall per sample); CPU: {cpu_model()}, nproc {cpu_cores()}")
 
 
 def run_reference(args, world, rank):
@@ -176,23 +242,26 @@ def run_reference(args, world, rank):
         return
     from synth import make_problem
 
-    prob = make_problem(args.workload, I=1)
-    n_freq = 4
+    prob = make_problem(args.workload)
+    workers = cpu_cores()
+    tasks = oracle_tasks(prob, workers)
+    pool = OraclePool(len(tasks))
     for _ in range(args.warmup):
-        oracle_sample(prob, n_freq)
+        pool.run(tasks)
     tot_t, tot_u = 0.0, 0.0
     for _ in range(args.steps):
-        dt, u = oracle_sample(prob, n_freq)
+        dt, u = pool.run(tasks)
         tot_t += dt
         tot_u += u
+    pool.close()
     value = tot_u / tot_t
-    sample = f"one C-ADMM iteration (10 LM x 4 PCG) of interval 0, first {n_freq} of {prob['P']} subbands, per step"
+    sample = oracle_sample_text(len(tasks), len(tasks), prob["P"], tot_t / args.steps) + ", per step"
     print(json.dumps({
         "impl": "reference", "metric": METRICS[args.workload], "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n_lm": N_LM, "n_cg": N_CG, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(tasks), "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -205,7 +274,10 @@ def run_ours(args, world, rank, local):
     from paper_1502_00858_gb300 import Calibrator, capi
     from synth import make_problem, user_layout
 
+    # the CPU baseline's worker processes start (spawn) while the GPU leg runs
+    pool = OraclePool(cpu_cores()) if (rank == 0 and not args.no_cpu_baseline) else None
     torch.cuda.set_device(local)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -293,18 +365,17 @@ def run_ours(args, world, rank, local):
     capi.calib_profile_enable(cal.ctx, False)
     dom = max((k for k in prof if prof[k]["bytes_per_launch"] > 0 and k != "stats_pass"), key=lambda k: prof[k]["total_ms"])
     avg_s = prof[dom]["total_ms"] / 1e3 / max(1, prof[dom]["launches"])
-    hbm_peak, fp32_peak, peak_kind = peaks()
+    hbm_peak, fp32_peak, peak_how = peaks(sms)
     hbm_achieved = prof[dom]["bytes_per_launch"] / avg_s / 1e9
     traffic = NCU_TRAFFIC.get((dom, source_hash(dom)))
     if dom in ALU_BOUND:
         achieved = prof[dom]["flops_per_launch"] / avg_s / 1e12
         roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": achieved / fp32_peak, "traffic": traffic,
-                    "peak_source": "FP32: 152 SMs x 128 lanes x 2 flops x max SM clock (" + peak_kind + " clock)",
+                    "frac": achieved / fp32_peak, "traffic": traffic, "peak_source": peak_how,
                     "hbm_achieved_gbs": hbm_achieved, "hbm_frac": hbm_achieved / hbm_peak}
     else:
         roofline = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
-                    "frac": hbm_achieved / hbm_peak, "traffic": traffic, "peak_source": peak_kind}
+                    "frac": hbm_achieved / hbm_peak, "traffic": traffic, "peak_source": peak_how}
     roofline["kernel"] = dom
     # the kernel that streams the visibilities: the statistics pass (HBM-bound), once per step
     sp = prof.get("stats_pass")
@@ -344,7 +415,7 @@ def run_ours(args, world, rank, local):
     roofline["residual_kernel"] = {"kernel": "residual", "bound": "hbm", "achieved": r_bytes / r_s / 1e9,
                                    "peak": hbm_peak, "unit": "GB/s", "frac": r_bytes / r_s / 1e9 / hbm_peak,
                                    "avg_launch_us": r_s * 1e6, "algorithmic_bytes_per_launch": r_bytes,
-                                   "traffic": None}
+                                   "traffic": NCU_TRAFFIC.get(("residual", source_hash("residual")))}
     del out_d
 
     # end to end through the public API with host buffers: H2D of the visibilities, uvw and sky,
@@ -374,14 +445,22 @@ def run_ours(args, world, rank, local):
     h2d = vis_h.numel() * 4 + uvw_h.numel() * 8 + sky_h.numel() * 8
     d2h = J_h.numel() * 4
 
+    cal.close()
+    stream_mb = (ul["vis"].nbytes + ul["coh"].nbytes) / 1e6
+    del vis_d, vis_h, ul
+
+    uneven = None
+    if not args.no_uneven and args.workload == WORKLOAD:
+        uneven = run_uneven(args, world, local, sms, hbm_peak, fp32_peak, barrier)
+
     cpu = None
-    if rank == 0 and not args.no_cpu_baseline:
-        os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
-        n_freq = 8
-        cdt, cu = oracle_sample(prob, n_freq)
-        cpu = {"value": cu / cdt, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"one C-ADMM iteration (10 LM x 4 PCG) of interval 0, first {n_freq} of {prob['P']} "
-                         f"subbands ({cdt:.1f} s)"}
+    if pool is not None:
+        tasks = oracle_tasks(prob, pool.workers)
+        pool.run(tasks[:1])  # workers have imported the oracle
+        cdt, cu = pool.run(tasks)
+        pool.close()
+        cpu = {"value": cu / cdt, "unit": UNIT, "cores": len(tasks), "kind": "oracle",
+               "sample": oracle_sample_text(pool.workers, len(tasks), prob["P"], cdt)}
 
     if rank == 0:
         out = {
@@ -398,7 +477,7 @@ def run_ours(args, world, rank, local):
                        "autotune_ms_hessian_trial": split_ms,
                        "step": f"predict + cold start + {n_admm} C-ADMM iterations",
                        "l2": f"inputs larger than L2: every step streams the visibilities and predicted coherencies "
-                             f"({(ul['vis'].nbytes + ul['coh'].nbytes) / 1e6:.0f} MB) through predict, the statistics "
+                             f"({stream_mb:.0f} MB) through predict, the statistics "
                              f"pass and the first residual sweep; each LM step reads U and S "
                              f"({1e-6 * prof['stats_trial']['bytes_per_launch']:.0f} MB)",
                        "parallelism": f"replica x{world}" if world > 1 else "single GPU",
@@ -408,11 +487,87 @@ def run_ours(args, world, rank, local):
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(launches),
             "clocks": clk,
+            "uneven": uneven,
         }
         print(json.dumps(out), flush=True)
-    cal.close()
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_uneven(args, world, local, sms, hbm_peak, fp32_peak, barrier) -> dict:
+    """The batched uneven workload (2560 agents: 256 subbands x 10 intervals, K=10, 5/10/20 samples
+    per subband, 0-15 % of baselines flagged, 50 C-ADMM iterations) in one graph per
+    calib_admm_iter, measured like the main line on fewer steps (one step takes seconds)."""
+    import torch
+
+    from paper_1502_00858_gb300 import Calibrator, capi
+    from synth import make_problem
+
+    t_gen = time.perf_counter()
+    prob = make_problem("uneven_n62_k10", seed=1 + int(os.environ.get("RANK", "0")), dtype=np.complex64,
+                        coherencies=False)
+    vis = np.concatenate([V.reshape(-1) for V in prob["V"]]).astype(np.complex64)
+    prob["V"] = None
+    t_gen = time.perf_counter() - t_gen
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream()
+    cal = Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
+                     n_intervals=prob["I"], samples=prob["T"], n_lm=N_LM, n_cg=N_CG, cuda_stream=stream.cuda_stream)
+    vis_d = torch.from_numpy(vis.view(np.float32)).to(dev)
+    del vis
+    uvw_d = torch.from_numpy(np.ascontiguousarray(prob["uvw"])).to(dev)
+    sky_d = torch.from_numpy(np.ascontiguousarray(prob["sky"])).to(dev)
+    flags_d = torch.from_numpy(np.ascontiguousarray(prob["flags"])).to(dev)
+    torch.cuda.synchronize()
+    capi.calib_set_data(cal.ctx, vis_d, flags=flags_d)
+    n_admm = prob["n_admm"]
+    keep = (prob["flags"] == 0).sum(axis=1)
+    per_iter_units = float(np.sum(keep * prob["T"])) * prob["K"]
+
+    def step():
+        capi.calib_predict(cal.ctx, uvw_d, sky_d, prob["f0"])
+        capi.calib_reset(cal.ctx)
+        capi.calib_admm_iter(cal.ctx, n_admm, want_hist=False)
+
+    step()  # warm-up: the autotuner and the graph capture run here
+    torch.cuda.synchronize()
+    steps = 2
+    launches0 = capi.calib_launch_count(cal.ctx)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    dt = e0.elapsed_time(e1) / 1e3
+    launches = capi.calib_launch_count(cal.ctx) - launches0
+    capi.calib_profile_enable(cal.ctx, True)
+    step()
+    prof = capi.calib_profile_read(cal.ctx)
+    capi.calib_profile_enable(cal.ctx, False)
+    cal.close()
+    per_kernel = {}
+    for k, v in prof.items():
+        if not v["launches"]:
+            continue
+        avg = v["total_ms"] / 1e3 / v["launches"]
+        e = {"avg_us": avg * 1e6, "launches": v["launches"]}
+        if v["flops_per_launch"] and k in ALU_BOUND:
+            e.update(bound="alu", achieved_tflops=v["flops_per_launch"] / avg / 1e12,
+                     frac=v["flops_per_launch"] / avg / 1e12 / fp32_peak)
+        elif v["bytes_per_launch"]:
+            e.update(bound="hbm", achieved_gbs=v["bytes_per_launch"] / avg / 1e9,
+                     frac=v["bytes_per_launch"] / avg / 1e9 / hbm_peak)
+        per_kernel[k] = e
+    return {"metric": METRICS["uneven_n62_k10"], "value": world * per_iter_units * n_admm * steps / dt,
+            "unit": UNIT, "ms_per_step": 1e3 * dt / steps, "steps": steps, "warmup": 1,
+            "agents": int(prob["A"]), "directions": int(prob["K"]), "admm_iters": n_admm,
+            "samples": sorted(set(int(t) for t in prob["T"])),
+            "flagged_fraction": round(float(np.mean(prob["flags"])), 4),
+            "gpu_launches": int(launches), "per_kernel": per_kernel, "generate_s": round(t_gen, 1),
+            "step": f"predict + cold start + {n_admm} C-ADMM iterations, one graph per calib_admm_iter"}
 
 
 def main():
@@ -426,6 +581,7 @@ def main():
     ap.add_argument("--formulation", choices=["statistics", "direct"], default="statistics")
     ap.add_argument("--workload", choices=sorted(METRICS), default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true", help="skip the nested batched uneven workload")
     ap.add_argument("--kernels-only", action="store_true",
                     help="run one launch of each sweep on the workload and exit (profiler captures)")
     args = ap.parse_args()

@@ -15,7 +15,7 @@ section's qualitative claims: the primal residual falls further for larger rho, 
 is lower for F = 2, distributed calibration has a lower error than normal calibration, the lowest
 error is at rho = 50, and F = 5 has higher error at the edge channels.
 
-    python -m paper_1502_00858_gb300.sim1 [--seed S] [--out FILE.json]
+    python -m experiments.sim1 [--seed S] [--out FILE.json]
 """
 from __future__ import annotations
 
@@ -82,7 +82,7 @@ def check_claims(res: dict) -> dict:
 
 def calibrate(prob: dict, ul: dict, basis: np.ndarray, rho: float, n_admm: int, n_lm: int):
     """One calibration of all channels through the library; returns (history, J [P,N,2,2])."""
-    from .calibrator import Calibrator
+    from paper_1502_00858_gb300 import Calibrator
 
     cal = Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], basis, np.full(prob["K"], rho),
                      n_intervals=prob["I"], samples=prob["T"], n_lm=n_lm, n_cg=N_CG)

@@ -64,18 +64,39 @@ typedef struct calib_ctx calib_ctx;
  *  CALIB_FORM_DIRECT      every pass streams the visibilities and coherencies sample by sample. */
 enum { CALIB_FORM_STATISTICS = 0, CALIB_FORM_DIRECT = 1 };
 
+/* The inner solver of the J-update (calib_options.jupdate), Eq. M1:
+ *  CALIB_JUPDATE_LM   n_lm Levenberg-Marquardt steps, each with n_cg preconditioned CG steps on the
+ *                     damped Gauss-Newton system (block-Jacobi preconditioner, Nielsen damping);
+ *  CALIB_JUPDATE_RTR  the paper's Riemannian trust-region method (Section 3, Appendix A) in
+ *                     Euclidean space (retraction J + eta): n_lm trust-region steps, each with up to
+ *                     n_cg truncated-CG steps (Steihaug-Toint, unpreconditioned, norm sqrt(h(x, x)),
+ *                     stopping on the boundary, on non-positive curvature or when
+ *                     ||r|| <= ||r0|| min(||r0||, 0.1)); step accepted when the ratio of actual to
+ *                     model decrease exceeds 0.1; radius quartered below 1/4, doubled (capped at
+ *                     ||J0||_h) above 3/4 when the CG stopped on the boundary; initial radius
+ *                     ||J0||_h / 8 at the start of every J-update;
+ *  CALIB_JUPDATE_SAGE the SAGE decomposition over directions (step D1): n_sage sweeps, each
+ *                     visiting k = 0 .. K-1; direction k's expectation step removes the other
+ *                     directions' models from the data (done exactly on the per-baseline statistics:
+ *                     U_k - sum_{l != k} S_kl J_pl J_ql^H, S_kk), and its maximisation step is the RTR
+ *                     above (n_lm steps of up to n_cg truncated-CG steps) on direction k's own
+ *                     Lagrangian with full regularisation. Needs CALIB_FORM_STATISTICS. */
+enum { CALIB_JUPDATE_LM = 0, CALIB_JUPDATE_RTR = 1, CALIB_JUPDATE_SAGE = 2 };
+
 typedef struct {
     int n_intervals;                   /* I >= 1 (default 1) */
     int n_samples;                     /* T >= 1: samples per agent when samples_per_agent is NULL */
     const int32_t* samples_per_agent;  /* [A] samples of each agent, or NULL (host pointer, copied) */
-    int n_lm;                          /* LM steps per J-update (default 10) */
-    int n_cg;                          /* PCG steps per LM step (default 4) */
+    int n_lm;                          /* LM (or trust-region) steps per J-update (default 10) */
+    int n_cg;                          /* PCG (or truncated-CG) steps per LM step (default 4) */
     int chunk_diagonals;               /* direct sweeps: baseline diagonals per CTA; 0 = automatic */
     void* cuda_stream;                 /* cudaStream_t to run on; NULL = the library creates one */
     int formulation;                   /* CALIB_FORM_STATISTICS (default) or CALIB_FORM_DIRECT */
     int ctas_per_sm;                   /* statistics sweeps: grid = SMs * ctas_per_sm CTAs (at most one
                                           per agent-diagonal), each taking an equal contiguous share of
                                           the (agent, diagonal) items; 0 = automatic */
+    int jupdate;                       /* CALIB_JUPDATE_LM (default), CALIB_JUPDATE_RTR or CALIB_JUPDATE_SAGE */
+    int n_sage;                        /* SAGE sweeps per J-update (default 1; CALIB_JUPDATE_SAGE only) */
 } calib_options;
 
 /* One record per C-ADMM iteration (Section 4 definitions, summed/averaged over all intervals):
@@ -154,6 +175,21 @@ int calib_admm_iter(calib_ctx* ctx, int n_iters, calib_stats* hist);
 /* Copy out J c64 [A][K][N][2][2], Z c128 [I][K][M][N][2][2], Y c64 [A][K][N][2][2].
  * Any pointer may be NULL. */
 int calib_get_solutions(calib_ctx* ctx, void* J, void* Z, void* Y, int ptr_kind);
+
+/* Checkpoint and resume of the iteration state (the paper restarts a calibration from the
+ * previous time slot's solutions, Section 3, initialisation; this keeps the whole C-ADMM state).
+ * The blob is opaque, host memory, and holds J, Y, B_i Z, Z, Z^{n-1}, the projected data gradient
+ * and Jacobi blocks at J, the per-agent LM scalars (L, g, damping), the pending first-iteration
+ * gauge-projection flag and the number of iterations since the last cold start; the data
+ * (visibilities, coherencies, flags) are not in it. After calib_set_state the next
+ * calib_admm_iter continues exactly (bit for bit) where the saved context stood.
+ *  calib_get_state: buf NULL -> *len receives the size needed; else *len is the buffer's size
+ *    (CALIB_EINVAL, with the size needed in *len, if too small) and receives the bytes written.
+ *    Synchronises the context's stream.
+ *  calib_set_state: CALIB_EINVAL if the blob is not one, or was saved for another shape,
+ *    formulation, station-pair list, sample counts or flags. Synchronises the stream. */
+int calib_get_state(calib_ctx* ctx, void* buf, size_t* len);
+int calib_set_state(calib_ctx* ctx, const void* buf, size_t len);
 
 /* Per-agent L_i and g_i after the last iteration, float64 [A] each (host). Either may be NULL. */
 int calib_get_agent_objective(calib_ctx* ctx, double* L, double* g);

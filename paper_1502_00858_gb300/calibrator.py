@@ -11,7 +11,8 @@ class Calibrator:
     basis [P,M], rho [K], I solution intervals, samples per agent."""
 
     def __init__(self, N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, samples=1, n_lm=10, n_cg=4,
-                 chunk_diagonals=0, cuda_stream=None, formulation=capi.CALIB_FORM_STATISTICS, ctas_per_sm=0):
+                 chunk_diagonals=0, cuda_stream=None, formulation=capi.CALIB_FORM_STATISTICS, ctas_per_sm=0,
+                 jupdate=capi.CALIB_JUPDATE_LM, n_sage=1):
         spa = None if np.isscalar(samples) else np.asarray(samples, dtype=np.int32)
         self.N, self.K, self.P = int(N), int(K), len(freqs_hz)
         self.M = int(np.asarray(basis).shape[1])
@@ -22,7 +23,8 @@ class Calibrator:
         self.ctx = capi.calib_init(N, pq, K, freqs_hz, basis, rho, n_intervals=n_intervals,
                                    n_samples=int(samples) if spa is None else 1, samples_per_agent=spa,
                                    n_lm=n_lm, n_cg=n_cg, chunk_diagonals=chunk_diagonals, cuda_stream=cuda_stream,
-                                   formulation=formulation, ctas_per_sm=ctas_per_sm)
+                                   formulation=formulation, ctas_per_sm=ctas_per_sm, jupdate=jupdate,
+                                   n_sage=n_sage)
 
     # shapes of the public arrays
     @property
@@ -69,6 +71,13 @@ class Calibrator:
         Y = np.zeros(self.jones_shape, dtype=np.complex64)
         capi.calib_get_solutions(self.ctx, J, Z, Y)
         return J, Z, Y
+
+    def get_state(self) -> bytes:
+        """Opaque checkpoint of the whole iteration state (calib_get_state)."""
+        return capi.calib_get_state(self.ctx)
+
+    def set_state(self, blob: bytes):
+        capi.calib_set_state(self.ctx, blob)
 
     def agent_objective(self):
         return capi.calib_get_agent_objective(self.ctx, self.A)

@@ -15,6 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libcalib.so")
 
 CALIB_FORM_STATISTICS, CALIB_FORM_DIRECT = 0, 1
+CALIB_JUPDATE_LM, CALIB_JUPDATE_RTR, CALIB_JUPDATE_SAGE = 0, 1, 2
 CALIB_OK, CALIB_EINVAL, CALIB_ERANK, CALIB_ENOMEM, CALIB_ECUDA, CALIB_ETIMEOUT, CALIB_ENUMERIC, CALIB_ESTATE = \
     0, -1, -2, -3, -4, -5, -6, -7
 
@@ -25,14 +26,14 @@ EXPORTED = [
     "calib_profile_read", "calib_launch_count", "calib_last_error", "calib_destroy", "calib_eval_noalloc",
     "calib_autotune", "calib_mlp_create", "calib_mlp_num_params", "calib_mlp_set_weights", "calib_mlp_get_weights",
     "calib_mlp_forward", "calib_mlp_grad", "calib_mlp_train_step", "calib_mlp_destroy", "calib_get_features",
-    "calib_warm_start", "calib_selftest_bounded_wait", "calib_residual",
+    "calib_warm_start", "calib_selftest_bounded_wait", "calib_residual", "calib_get_state", "calib_set_state",
 ]
 
 
 class CalibOptions(C.Structure):
     _fields_ = [("n_intervals", C.c_int), ("n_samples", C.c_int), ("samples_per_agent", C.POINTER(C.c_int32)),
                 ("n_lm", C.c_int), ("n_cg", C.c_int), ("chunk_diagonals", C.c_int), ("cuda_stream", C.c_void_p),
-                ("formulation", C.c_int), ("ctas_per_sm", C.c_int)]
+                ("formulation", C.c_int), ("ctas_per_sm", C.c_int), ("jupdate", C.c_int), ("n_sage", C.c_int)]
 
 
 class CalibStats(C.Structure):
@@ -92,6 +93,8 @@ def load(path: str = LIB_PATH):
         "calib_warm_start": (i, [vp, vp, vp, vp, vp, i]),
         "calib_selftest_bounded_wait": (i, [i, vp, vp]),
         "calib_residual": (i, [vp, vp, i, vp, i]),
+        "calib_get_state": (i, [vp, vp, C.POINTER(C.c_size_t)]),
+        "calib_set_state": (i, [vp, vp, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -137,7 +140,7 @@ def calib_default_options() -> CalibOptions:
 
 def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, samples_per_agent=None,
                n_lm=10, n_cg=4, chunk_diagonals=0, cuda_stream=None, formulation=CALIB_FORM_STATISTICS,
-               ctas_per_sm=0):
+               ctas_per_sm=0, jupdate=CALIB_JUPDATE_LM, n_sage=1):
     lib = load()
     pq_a = np.ascontiguousarray(pq, dtype=np.int32)
     fr = np.ascontiguousarray(freqs_hz, dtype=np.float64)
@@ -148,6 +151,8 @@ def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, sa
     opt.chunk_diagonals = chunk_diagonals
     opt.formulation = formulation
     opt.ctas_per_sm = ctas_per_sm
+    opt.jupdate = jupdate
+    opt.n_sage = n_sage
     spa = None
     if samples_per_agent is not None:
         spa = np.ascontiguousarray(samples_per_agent, dtype=np.int32)
@@ -188,6 +193,20 @@ def calib_residual(ctx, out, subtract=None, correct: int = -1):
     p, k, _ = _ptr(out)
     _check(load().calib_residual(ctx, sp, int(correct), p, k))
     return out
+
+
+def calib_get_state(ctx) -> bytes:
+    """The context's opaque iteration-state blob (host bytes)."""
+    n = C.c_size_t(0)
+    _check(load().calib_get_state(ctx, None, C.byref(n)))
+    buf = C.create_string_buffer(n.value)
+    _check(load().calib_get_state(ctx, buf, C.byref(n)))
+    return buf.raw[:n.value]
+
+
+def calib_set_state(ctx, blob: bytes) -> None:
+    buf = C.create_string_buffer(bytes(blob), len(blob))
+    _check(load().calib_set_state(ctx, buf, len(blob)))
 
 
 def calib_reset(ctx):

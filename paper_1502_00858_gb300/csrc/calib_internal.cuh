@@ -58,14 +58,21 @@ struct DiagDesc {     // one per (agent, diagonal)
 struct AgentState {   // per-agent scalars
     double L, g;      // augmented Lagrangian and data cost at the current J
     double L_t, g_t;  // at the LM trial point
-    double rz;        // PCG r.z
-    double pred;      // predicted decrease of the LM step
+    double rz;        // PCG r.z (truncated CG: h(r, r))
+    double pred;      // predicted decrease of the LM (or trust-region) step
     double mu, nu;    // LM damping
-    int cg_stop;      // PCG stopped (r.z <= 0 or p.Ap <= 0)
+    int cg_stop;      // PCG stopped (r.z <= 0 or p.Ap <= 0); truncated CG: a TCG_STOP_* reason
     int accepted;     // LM steps accepted (cumulative)
     int rejected;     // LM steps rejected (cumulative)
     int pad_;
+    // Riemannian trust region (RTR J-update)
+    double delta, delta_bar;  // trust-region radius and its cap ||J0||_h
+    double r0sq;              // h(r0, r0) of the current truncated CG
+    double ee;                // h(eta, eta) of the current truncated-CG iterate
 };
+
+// Why a truncated-CG solve stopped (AgentState.cg_stop in the RTR J-update).
+enum TcgStop : int { TCG_RUNNING = 0, TCG_BOUNDARY = 1, TCG_CURVATURE = 2, TCG_RESIDUAL = 3 };
 
 // Arguments of a baseline sweep (residual/gradient pass or Gauss-Newton Hessian-vector pass).
 struct SweepArgs {
@@ -122,12 +129,31 @@ int sweep_tile_samples(int slots_max, int K, bool hessvec);
 int sweep_threads(int slots_max);
 
 // ---- launchers (lm.cu)
-enum LMEvalMode : int { LM_BEGIN_FROM_PARTIALS = 0, LM_BEGIN_REUSE = 1, LM_ACCEPT = 2 };
+// LM_BEGIN_FROM_TRIAL (trust region only): the gradient comes from the partials of a statistics
+// trial pass run at J' = J, which carries no absolute cost (the SAGE sub-problems use decreases only).
+enum LMEvalMode : int { LM_BEGIN_FROM_PARTIALS = 0, LM_BEGIN_REUSE = 1, LM_ACCEPT = 2, LM_BEGIN_FROM_TRIAL = 3 };
 cudaError_t launch_lm_eval(const LMArgs& a, int mode, cudaStream_t s);
 // One PCG step; with last set it also forms the LM trial point Jt = J + x and the predicted decrease.
 cudaError_t launch_cg_step(const LMArgs& a, bool last, cudaStream_t s);
 cudaError_t launch_eval_output(const LMArgs& a, float* grad_out, double* L_out, double* g_out, cudaStream_t s);
+// Riemannian trust-region J-update (the paper's inner solver): one truncated-CG step after the
+// Hessian sweep of its direction d (with last set it also forms J' = J + eta and the predicted
+// decrease), and the trust-region bookkeeping after a residual or trial sweep (modes in LMEvalMode).
+cudaError_t launch_tcg_step(const LMArgs& a, bool last, cudaStream_t s);
+cudaError_t launch_rtr_eval(const LMArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_hv_output(const LMArgs& a, float* out, cudaStream_t s);
+
+// ---- launchers (sage.cu): the SAGE decomposition of the J-update over directions (step D1)
+struct SageArgs {
+    const float2* U; const float2* S;       // statistics of all directions (full circulant layout)
+    const float* J; const float* Y; const float* BZ;  // [A][K][N][8]
+    float* J_out;                           // where direction k's solution is scattered back (= J)
+    float2* U1; float2* S1;                 // direction k's one-direction statistics
+    float *J1, *Jt1, *Y1, *BZ1;             // [A][N][8] copies of direction k's vectors
+    int A, D, NP, K, N;
+};
+cudaError_t launch_sage_prepare(const SageArgs& g, int k, cudaStream_t s);
+cudaError_t launch_sage_scatter(const SageArgs& g, int k, cudaStream_t s);
 
 // ---- launchers (consensus.cu)
 cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s);

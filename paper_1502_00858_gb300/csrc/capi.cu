@@ -79,6 +79,8 @@ struct calib_ctx {
     int dev = 0;
     int N = 0, B = 0, K = 0, P = 0, M = 0, I = 0, A = 0, D = 0;
     int n_lm = 10, n_cg = 4, chunk_diags = 1, n_chunks = 1, slots_max = 4;
+    int jupdate = 0;               // CALIB_JUPDATE_LM, CALIB_JUPDATE_RTR or CALIB_JUPDATE_SAGE
+    int n_sage = 1;                // SAGE sweeps over the directions per J-update
     bool tune_pending = false;     // work split chosen by the autotuner at the first iteration
     // statistics sweeps: grid = sms * m CTAs (at most A*D), balanced contiguous item ranges; the
     // Hessian and trial passes are split independently
@@ -137,12 +139,18 @@ struct calib_ctx {
     double* evG = nullptr;
     void* staging = nullptr;
     size_t staging_bytes = 0;
+    // SAGE: one direction's one-direction problem (statistics and per-agent vectors, K = 1)
+    float2 *sgU = nullptr, *sgS = nullptr;
+    float *sgJ = nullptr, *sgJt = nullptr, *sgY = nullptr, *sgBZ = nullptr, *sgGradg = nullptr, *sgGrad = nullptr;
+    float *sgX = nullptr, *sgR = nullptr, *sgP = nullptr, *sgGm = nullptr;
+    AgentState* sgSt = nullptr;
     float *ws_prev = nullptr, *ws_mlp = nullptr;   // warm start: previous J, network J
     double *ws_L = nullptr, *xf_d = nullptr;         // [2A] L at both starts; [A] normalised frequency
     int* ws_chose = nullptr;
 
     bool data_set = false, coh_set = false;
     bool cold = true, need_eval = true;
+    long long iters_done = 0;  // C-ADMM iterations since the last cold start or warm state
 
     std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;
     long long launches = 0;
@@ -231,6 +239,57 @@ SSArgs ss_args(calib_ctx* c, const float* J, const float* eta, bool hessvec) {
     a.NP = (c->N + 3) / 4 * 4;
     a.part_stride = hessvec ? c->part_hv.stride : c->part_tr.stride;
     return a;
+}
+
+// The one-direction problem of direction k in the SAGE J-update: its statistics and vectors (K = 1).
+SSArgs sage_ss_args(calib_ctx* c, bool hessvec) {
+    SSArgs a = ss_args(c, c->sgJ, hessvec ? c->sgP : c->sgJt, hessvec);
+    a.U = c->sgU;
+    a.S = c->sgS;
+    a.K = 1;
+    return a;
+}
+
+LMArgs sage_lm_args(calib_ctx* c, PartsFrom from, int k) {
+    LMArgs a = lm_args(c, from);
+    a.J = c->sgJ;
+    a.Jt = c->sgJt;
+    a.Y = c->sgY;
+    a.BZ = c->sgBZ;
+    a.gradg = c->sgGradg;
+    a.grad = c->sgGrad;
+    a.x = c->sgX;
+    a.r = c->sgR;
+    a.p = c->sgP;
+    a.Gm = c->sgGm;
+    a.gw = nullptr;  // the trust-region kernels use no Jacobi blocks
+    a.st = c->sgSt;
+    a.rho = c->rho_d + k;
+    a.K = 1;
+    a.cost_from_decrease = 1;
+    return a;
+}
+
+SageArgs sage_args(calib_ctx* c) {
+    SageArgs g{};
+    g.U = c->ssU;
+    g.S = c->ssS;
+    g.J = c->J;
+    g.Y = c->Y;
+    g.BZ = c->BZ;
+    g.J_out = c->J;
+    g.U1 = c->sgU;
+    g.S1 = c->sgS;
+    g.J1 = c->sgJ;
+    g.Jt1 = c->sgJt;
+    g.Y1 = c->sgY;
+    g.BZ1 = c->sgBZ;
+    g.A = c->A;
+    g.D = c->D;
+    g.NP = (c->N + 3) / 4 * 4;
+    g.K = c->K;
+    g.N = c->N;
+    return g;
 }
 
 // Split the A*D items of the statistics sweeps over grid = min(A*D, sms * m) CTAs and record how
@@ -507,14 +566,15 @@ struct Enq {
             ge->prof.push_back(pp);
         }
     }
+    // the inner solver's per-agent kernels: PCG / LM damping, or truncated CG / trust region
     void cg_step(const LMArgs& la, bool last) {
         ProfPair pp = begin(4);
-        ok(launch_cg_step(la, last, c->stream));
+        ok(c->jupdate == CALIB_JUPDATE_RTR ? launch_tcg_step(la, last, c->stream) : launch_cg_step(la, last, c->stream));
         end(pp);
     }
     void lm_eval(const LMArgs& la, int mode) {
         ProfPair pp = begin(5);
-        ok(launch_lm_eval(la, mode, c->stream));
+        ok(c->jupdate == CALIB_JUPDATE_RTR ? launch_rtr_eval(la, mode, c->stream) : launch_lm_eval(la, mode, c->stream));
         end(pp);
     }
     void sweep(int mode, const float* J, const float* eta) {
@@ -531,8 +591,45 @@ struct Enq {
     }
 };
 
+// SAGE J-update (step D1): n_sage sweeps over the directions; direction k's one-direction problem
+// (expectation step on the statistics, sage.cu) is solved by n_lm trust-region steps starting from
+// the gradient of a trial pass at J' = J; its solution is written back before the next direction.
+// Then the whole problem's data cost, gradient and Jacobi blocks at the new J (the records).
+void enqueue_sage_jupdate(Enq& q) {
+    calib_ctx* c = q.c;
+    const SageArgs sg = sage_args(c);
+    const SSArgs hv1 = sage_ss_args(c, true), tr1 = sage_ss_args(c, false);
+    for (int sweep = 0; sweep < c->n_sage; ++sweep)
+        for (int k = 0; k < c->K; ++k) {
+            const LMArgs lh = sage_lm_args(c, PARTS_SS_HESSIAN, k), lt = sage_lm_args(c, PARTS_SS_TRIAL, k);
+            q.ok(launch_sage_prepare(sg, k, c->stream));
+            q.ok(launch_ss_sweep(tr1, false, c->part_tr.grid, c->stream));
+            q.ok(launch_rtr_eval(lt, LM_BEGIN_FROM_TRIAL, c->stream));
+            for (int l = 0; l < c->n_lm; ++l) {
+                for (int j = 0; j < c->n_cg; ++j) {
+                    q.ok(launch_ss_sweep(hv1, true, c->part_hv.grid, c->stream));
+                    q.ok(launch_tcg_step(lh, j == c->n_cg - 1, c->stream));
+                }
+                q.ok(launch_ss_sweep(tr1, false, c->part_tr.grid, c->stream));
+                q.ok(launch_rtr_eval(lt, LM_ACCEPT, c->stream));
+            }
+            q.ok(launch_sage_scatter(sg, k, c->stream));
+        }
+    q.ok(launch_sweep(sweep_args(c, SWEEP_RESIDUAL, c->J, nullptr), SWEEP_RESIDUAL, c->stream));
+    q.ok(launch_lm_eval(lm_args(c, PARTS_DIRECT), LM_BEGIN_FROM_PARTIALS, c->stream));
+}
+
 void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
     calib_ctx* c = q.c;
+    if (c->jupdate == CALIB_JUPDATE_SAGE) {
+        const ConsArgs ca = cons_args(c);
+        enqueue_sage_jupdate(q);
+        if (gauge) q.ok(launch_gauge(ca, c->stream));
+        q.ok(launch_zupdate(ca, c->stream));
+        q.ok(launch_yupdate(ca, c->stream));
+        q.ok(launch_stats(ca, c->stream));
+        return;
+    }
     const bool ssf = c->formulation == 0;
     const LMArgs la_hv = lm_args(c, ssf ? PARTS_SS_HESSIAN : PARTS_DIRECT);  // after a Hessian sweep
     const LMArgs la = lm_args(c, ssf ? PARTS_SS_TRIAL : PARTS_DIRECT);       // after the trial sweep
@@ -712,6 +809,8 @@ void calib_default_options(calib_options* opt) {
     opt->cuda_stream = nullptr;
     opt->formulation = CALIB_FORM_STATISTICS;
     opt->ctas_per_sm = 0;
+    opt->jupdate = CALIB_JUPDATE_LM;
+    opt->n_sage = 1;
 }
 
 int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* pq, int n_dirs, int n_freqs,
@@ -734,6 +833,11 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     if (opt.n_lm < 1 || opt.n_cg < 1) return fail(CALIB_EINVAL, "n_lm and n_cg must be >= 1");
     if (opt.formulation != CALIB_FORM_STATISTICS && opt.formulation != CALIB_FORM_DIRECT)
         return fail(CALIB_EINVAL, "formulation must be CALIB_FORM_STATISTICS or CALIB_FORM_DIRECT");
+    if (opt.jupdate != CALIB_JUPDATE_LM && opt.jupdate != CALIB_JUPDATE_RTR && opt.jupdate != CALIB_JUPDATE_SAGE)
+        return fail(CALIB_EINVAL, "jupdate must be CALIB_JUPDATE_LM, CALIB_JUPDATE_RTR or CALIB_JUPDATE_SAGE");
+    if (opt.jupdate == CALIB_JUPDATE_SAGE && opt.formulation != CALIB_FORM_STATISTICS)
+        return fail(CALIB_EINVAL, "CALIB_JUPDATE_SAGE needs CALIB_FORM_STATISTICS");
+    if (opt.jupdate == CALIB_JUPDATE_SAGE && opt.n_sage < 1) return fail(CALIB_EINVAL, "n_sage must be >= 1");
     std::vector<char> seen((size_t)N * N, 0);
     for (int b = 0; b < B; ++b) {
         const int p = pq[2 * b], q = pq[2 * b + 1];
@@ -761,6 +865,8 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     c->n_lm = opt.n_lm;
     c->n_cg = opt.n_cg;
     c->formulation = opt.formulation;
+    c->jupdate = opt.jupdate;
+    c->n_sage = opt.jupdate == CALIB_JUPDATE_SAGE ? opt.n_sage : 1;
     c->pq.assign(pq, pq + 2 * (size_t)B);
     c->freqs.assign(freqs_hz, freqs_hz + P);
     c->basis.assign(basis, basis + (size_t)P * M);
@@ -832,6 +938,14 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess && dalloc(&c->part_hv.pn, (size_t)A) == cudaSuccess &&
           dalloc(&c->part_tr.pn, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->vis_off_d, (size_t)A) == cudaSuccess && dalloc(&c->coh_off_d, (size_t)A) == cudaSuccess;
+    if (c->jupdate == CALIB_JUPDATE_SAGE) {
+        const size_t npos = (size_t)A * c->D * ((N + 3) / 4 * 4), v1 = (size_t)A * N * 8;
+        okm = okm && dalloc(&c->sgU, npos * 4) == cudaSuccess && dalloc(&c->sgS, npos) == cudaSuccess;
+        for (float** pp : {&c->sgJ, &c->sgJt, &c->sgY, &c->sgBZ, &c->sgGradg, &c->sgGrad, &c->sgX, &c->sgR, &c->sgP})
+            okm = okm && dalloc(pp, v1) == cudaSuccess;
+        okm = okm && dalloc(&c->sgGm, (size_t)A * N * 4) == cudaSuccess && dalloc(&c->sgSt, (size_t)A) == cudaSuccess;
+        if (okm) cudaMemset(c->sgSt, 0, (size_t)A * sizeof(AgentState));
+    }
     if (!okm) return bail(fail(CALIB_ENOMEM, "device allocation failed"));
     if (ensure_stats(c, 64) != CALIB_OK) return bail(CALIB_ENOMEM);
     cudaMemcpy(c->basis_d, c->basis.data(), c->basis.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -870,6 +984,7 @@ int calib_reset(calib_ctx* c) {
     c->launches += 1;
     c->cold = true;
     c->need_eval = true;
+    c->iters_done = 0;
     return CALIB_OK;
 }
 
@@ -1078,6 +1193,7 @@ int calib_set_consensus(calib_ctx* c, const void* Zin, const void* Yin, int ptr_
     CK(launch_bz_only(ca, c->stream));
     c->launches += 1;
     c->cold = false;
+    c->iters_done = 0;
     c->need_eval = true;
     if (ptr_kind == 0) CK(cudaStreamSynchronize(c->stream));
     return CALIB_OK;
@@ -1140,6 +1256,7 @@ int calib_admm_iter(calib_ctx* c, int n_iters, calib_stats* hist) {
     c->launches += it->second.kernels;
     c->need_eval = false;
     c->cold = false;
+    c->iters_done += n_iters;
     CK(cudaStreamSynchronize(c->stream));
     rc = check_status(c);
     if (rc) return rc;
@@ -1161,6 +1278,115 @@ int calib_admm_iter(calib_ctx* c, int n_iters, calib_stats* hist) {
             hist[i].resid_norm = h[(size_t)i * 4 + 3];
         }
     }
+    return CALIB_OK;
+}
+
+namespace {
+
+// Checkpoint blob: a fixed header, then the device arrays in a fixed order (each starting on a
+// 64-byte boundary of the blob). Everything a following calib_admm_iter reads from the previous
+// one is here, so a resume continues with the same bits.
+struct StateHeader {
+    char magic[8];          // "CALIBST1"
+    int32_t version;        // 1
+    int32_t N, B, K, P, M, I, A, formulation;
+    int32_t cold;           // the next iteration applies the first-iteration gauge projection
+    int32_t need_eval;      // the next iteration starts with a residual sweep at J
+    int64_t iters_done;     // C-ADMM iterations since the last cold start or warm state
+    uint64_t pair_hash;     // FNV-1a of the station pairs and the flags: the data layout
+    int64_t total_bytes;
+};
+
+uint64_t fnv1a(const void* p, size_t n, uint64_t h) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+    return h;
+}
+
+uint64_t layout_hash(calib_ctx* c) {
+    uint64_t h = fnv1a(c->pq.data(), c->pq.size() * sizeof(int32_t), 1469598103934665603ull);
+    h = fnv1a(c->T.data(), c->T.size() * sizeof(int), h);
+    return c->flags_h.empty() ? h : fnv1a(c->flags_h.data(), c->flags_h.size(), h);
+}
+
+struct StatePart { void* dev; size_t bytes; };
+
+std::vector<StatePart> state_parts(calib_ctx* c) {
+    const size_t vb = (size_t)c->A * c->K * c->N * 8 * sizeof(float);
+    const size_t gb = (size_t)c->A * c->K * c->N * 4 * sizeof(float);
+    const size_t zb = (size_t)c->I * c->K * c->M * c->N * 8 * sizeof(double);
+    return {{c->J, vb}, {c->Y, vb}, {c->BZ, vb}, {c->gradg, vb}, {c->Gm, gb},
+            {c->Z, zb}, {c->Zprev, zb}, {c->st, (size_t)c->A * sizeof(AgentState)}};
+}
+
+size_t round64(size_t x) { return (x + 63) / 64 * 64; }
+
+size_t state_bytes(calib_ctx* c) {
+    size_t n = round64(sizeof(StateHeader));
+    for (const StatePart& sp : state_parts(c)) n += round64(sp.bytes);
+    return n;
+}
+
+}  // namespace
+
+int calib_get_state(calib_ctx* c, void* buf, size_t* len) {
+    if (!c || !len) return fail(CALIB_EINVAL, "ctx and len are required");
+    const size_t need = state_bytes(c);
+    if (!buf) {
+        *len = need;
+        return CALIB_OK;
+    }
+    if (*len < need) {
+        *len = need;
+        return fail(CALIB_EINVAL, "state buffer too small (*len now holds the size needed)");
+    }
+    StateHeader h{};
+    std::memcpy(h.magic, "CALIBST1", 8);
+    h.version = 1;
+    h.N = c->N; h.B = c->B; h.K = c->K; h.P = c->P; h.M = c->M; h.I = c->I; h.A = c->A;
+    h.formulation = c->formulation;
+    h.cold = c->cold ? 1 : 0;
+    h.need_eval = c->need_eval ? 1 : 0;
+    h.iters_done = c->iters_done;
+    h.pair_hash = layout_hash(c);
+    h.total_bytes = (int64_t)need;
+    unsigned char* out = static_cast<unsigned char*>(buf);
+    std::memset(out, 0, need);
+    std::memcpy(out, &h, sizeof(h));
+    size_t off = round64(sizeof(StateHeader));
+    for (const StatePart& sp : state_parts(c)) {
+        CK(cudaMemcpyAsync(out + off, sp.dev, sp.bytes, cudaMemcpyDeviceToHost, c->stream));
+        off += round64(sp.bytes);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    *len = need;
+    return CALIB_OK;
+}
+
+int calib_set_state(calib_ctx* c, const void* buf, size_t len) {
+    if (!c || !buf) return fail(CALIB_EINVAL, "ctx and buf are required");
+    StateHeader h{};
+    if (len < sizeof(h)) return fail(CALIB_EINVAL, "state blob too short");
+    std::memcpy(&h, buf, sizeof(h));
+    if (std::memcmp(h.magic, "CALIBST1", 8) != 0 || h.version != 1)
+        return fail(CALIB_EINVAL, "not a calibration state blob (magic or version)");
+    if (h.N != c->N || h.B != c->B || h.K != c->K || h.P != c->P || h.M != c->M || h.I != c->I || h.A != c->A ||
+        h.formulation != c->formulation)
+        return fail(CALIB_EINVAL, "state blob was saved for another problem shape or formulation");
+    if (h.pair_hash != layout_hash(c))
+        return fail(CALIB_EINVAL, "state blob was saved for other station pairs, samples or flags");
+    const size_t need = state_bytes(c);
+    if ((size_t)h.total_bytes != need || len < need) return fail(CALIB_EINVAL, "state blob has the wrong size");
+    const unsigned char* in = static_cast<const unsigned char*>(buf);
+    size_t off = round64(sizeof(StateHeader));
+    for (const StatePart& sp : state_parts(c)) {
+        CK(cudaMemcpyAsync(sp.dev, in + off, sp.bytes, cudaMemcpyHostToDevice, c->stream));
+        off += round64(sp.bytes);
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    c->cold = h.cold != 0;
+    c->need_eval = h.need_eval != 0;
+    c->iters_done = h.iters_done;
     return CALIB_OK;
 }
 
@@ -1339,6 +1565,7 @@ int calib_warm_start(calib_ctx* c, calib_mlp* mlp, const void* J_prev, const voi
     }
     c->need_eval = true;
     c->cold = false;
+    c->iters_done = 0;
     if (ptr_kind == 0) CK(cudaStreamSynchronize(c->stream));
     return CALIB_OK;
 }
@@ -1410,7 +1637,9 @@ void calib_destroy(calib_ctx* c) {
                     (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->dual2, (void*)c->stats, (void*)c->iter_counter,
                     (void*)c->status, (void*)c->part_hv.pn, (void*)c->part_tr.pn, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
                     (void*)c->coh_off_d, c->staging, (void*)c->ws_prev, (void*)c->ws_mlp, (void*)c->ws_L,
-                    (void*)c->xf_d, (void*)c->ws_chose})
+                    (void*)c->xf_d, (void*)c->ws_chose, (void*)c->sgU, (void*)c->sgS, (void*)c->sgJ, (void*)c->sgJt,
+                    (void*)c->sgY, (void*)c->sgBZ, (void*)c->sgGradg, (void*)c->sgGrad, (void*)c->sgX, (void*)c->sgR,
+                    (void*)c->sgP, (void*)c->sgGm, (void*)c->sgSt})
         if (p) cudaFree(p);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;

@@ -613,6 +613,284 @@ __global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_cg_step(co
     }
 }
 
+// ---- Riemannian trust region (the paper's inner solver for Eq. M1, Section 3 and Appendix A)
+//
+// In Euclidean space the retraction is J + eta and the Riemannian gradient and Hessian are grad L
+// (Eq. gradL) and Hess L (Eq. HessL, Gauss-Newton part), so one RTR step is: truncated CG
+// (Steihaug-Toint, no preconditioner, norm ||x||_h = sqrt(h(x, x))) on the model
+// m(eta) = h(grad, eta) + 1/2 h(eta, Hess L[eta]) within the radius Delta, then the ratio
+// rho = (L(J) - L(J + eta)) / (m(0) - m(eta)) decides the step and the radius (Absil, Baker and
+// Gallivan 2007): accept when rho > 0.1; Delta /= 4 when rho < 1/4; Delta = min(2 Delta, Delta_bar)
+// when rho > 3/4 and the CG stopped on the boundary. Delta_bar = ||J0||_h at the start of the
+// J-update, Delta_0 = Delta_bar / 8. The CG stops on the boundary, on non-positive curvature
+// (both then step to the boundary along d), when ||r|| <= ||r0|| min(||r0||, 0.1), or after n_cg
+// steps. Sign convention as in PCG: r = b - Hess L[eta] with b = -grad, d_0 = r_0, so the model
+// decrease is m(0) - m(eta) = 1/2 h(eta, b + r), formed from the CG residual without another sweep.
+constexpr double TCG_KAPPA = 0.1;   // residual test ||r|| <= ||r0|| min(||r0||, kappa)
+constexpr double RTR_ACCEPT = 0.1;  // a step is accepted when its ratio exceeds this
+
+// One truncated-CG step of one agent after the Hessian sweep of its direction d (in a.p); with
+// last set, also J' = J + eta and the predicted decrease 1/2 h(eta, b + r).
+template <int BPT>
+__global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_tcg_step(const LMArgs a, const int last) {
+    // one area per reduction call site (block_sum<NV> uses NV * 32 floats)
+    __shared__ float red_d[3 * 32], red_r[32], red_p[32];
+    const int agent = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
+    const int N = a.N, KN = a.K * N;
+    const size_t off = (size_t)agent * KN * 8;
+    AgentState& st = a.st[agent];
+    Blk x[BPT], r[BPT], p[BPT], ap[BPT];  // eta, r, d; ap: the Hessian partial sum, then Hess L[d]
+    float lam[BPT];
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int blk = tid + i * T;
+        x[i] = r[i] = p[i] = ap[i] = zero_blk();
+        lam[i] = 0.f;
+        if (blk >= KN) continue;
+        x[i] = ld_blk(a.x + off, blk);
+        r[i] = ld_blk(a.r + off, blk);
+        p[i] = ld_blk(a.p + off, blk);
+        ap[i] = sum_parts(a, agent, blk, KN);
+        lam[i] = 0.5f * a.rho[blk / N];
+    }
+    // the agent's scalars, read before any thread can write them
+    const int stop = st.cg_stop;
+    const double rr = st.rz, ee = st.ee, delta = st.delta, r0sq = st.r0sq;
+    if (stop == TCG_RUNNING) {
+        float v[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            if (tid + i * T >= KN) continue;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) ap[i].v[e] = fmaf(lam[i], p[i].v[e], ap[i].v[e]);
+            v[0] += dot8(p[i], ap[i]);
+            v[1] += dot8(x[i], p[i]);
+            v[2] += dot8(p[i], p[i]);
+        }
+        block_sum<3>(v, red_d);
+        const double dHd = 2.0 * v[0], ed = 2.0 * v[1], dd = 2.0 * v[2];  // h(d, Hd), h(eta, d), h(d, d)
+        int why = TCG_RUNNING;
+        double step = 0.0, ee_new = ee;
+        if (!(dHd > 0.0)) {
+            why = TCG_CURVATURE;
+        } else {
+            step = rr / dHd;
+            ee_new = ee + 2.0 * step * ed + step * step * dd;
+            if (ee_new >= delta * delta) why = TCG_BOUNDARY;
+        }
+        if (why != TCG_RUNNING) {  // to the boundary along d: ||eta + tau d||_h = Delta, tau >= 0
+            step = (dd > 0.0) ? (-ed + sqrt(fmax(ed * ed + dd * (delta * delta - ee), 0.0))) / dd : 0.0;
+            ee_new = delta * delta;
+        }
+        const float sf = (float)step;
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            if (tid + i * T >= KN) continue;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                x[i].v[e] = fmaf(sf, p[i].v[e], x[i].v[e]);
+                r[i].v[e] = fmaf(-sf, ap[i].v[e], r[i].v[e]);
+            }
+        }
+        double rr_new = rr;
+        if (why == TCG_RUNNING) {
+            float w[1] = {0.f};
+#pragma unroll
+            for (int i = 0; i < BPT; ++i)
+                if (tid + i * T < KN) w[0] += dot8(r[i], r[i]);
+            block_sum<1>(w, red_r);
+            rr_new = 2.0 * w[0];
+            if (rr_new <= r0sq * fmin(r0sq, TCG_KAPPA * TCG_KAPPA)) {
+                why = TCG_RESIDUAL;
+            } else {
+                const float beta = (float)(rr_new / rr);
+#pragma unroll
+                for (int i = 0; i < BPT; ++i) {
+                    if (tid + i * T >= KN) continue;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) p[i].v[e] = fmaf(beta, p[i].v[e], r[i].v[e]);
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            const int blk = tid + i * T;
+            if (blk >= KN) continue;
+            st_blk(a.x + off, blk, x[i]);
+            st_blk(a.r + off, blk, r[i]);
+            st_blk(a.p + off, blk, p[i]);
+        }
+        if (tid == 0) {
+            st.rz = rr_new;
+            st.ee = ee_new;
+            st.cg_stop = why;
+        }
+    }
+    if (last) {
+        float v[1] = {0.f};
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            const int blk = tid + i * T;
+            if (blk >= KN) continue;
+            const Blk jb = ld_blk(a.J + off, blk), gr = ld_blk(a.grad + off, blk);
+            Blk jt;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                jt.v[e] = jb.v[e] + x[i].v[e];
+                v[0] = fmaf(x[i].v[e], r[i].v[e] - gr.v[e], v[0]);
+            }
+            st_blk(a.Jt + off, blk, jt);
+        }
+        block_sum<1>(v, red_p);
+        if (tid == 0) st.pred = (double)v[0];  // 1/2 h(eta, b + r), h = 2 * dot
+    }
+}
+
+// Trust-region bookkeeping of one agent after a residual or trial sweep (modes in LMEvalMode), then
+// the start of the next truncated CG: grad = gradg + Y/2 + rho/2 (J - BZ), r = d = -grad, eta = 0.
+// The begin modes set Delta_bar = ||J||_h and Delta = Delta_bar / 8.
+template <int BPT>
+__global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_rtr_eval(const LMArgs a, const int mode) {
+    extern __shared__ __align__(16) float sm[];  // KN*GT floats (gauge terms)
+    __shared__ float red[4][64];
+    __shared__ float Asol[MAX_K * 4];
+    __shared__ int accept_s;
+    const int agent = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
+    const int N = a.N, K = a.K, KN = K * N;
+    const size_t off = (size_t)agent * KN * 8;
+    AgentState& st = a.st[agent];
+
+    Blk j[BPT], y[BPT], bz[BPT], gg[BPT];
+    float rk[BPT];
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int blk = tid + i * T;
+        j[i] = y[i] = bz[i] = gg[i] = zero_blk();
+        rk[i] = 0.f;
+        if (blk < KN) {
+            j[i] = ld_blk(a.J + off, blk);
+            y[i] = ld_blk(a.Y + off, blk);
+            bz[i] = ld_blk(a.BZ + off, blk);
+            rk[i] = a.rho[blk / N];
+        }
+    }
+    bool fresh = false;
+    if (mode == LM_ACCEPT) {  // the trial sweep just ran at J' = J + eta
+        Blk jt[BPT];
+        float v[2] = {0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            const int blk = tid + i * T;
+            jt[i] = zero_blk();
+            if (blk < KN) {
+                jt[i] = ld_blk(a.Jt + off, blk);
+                v[0] += penalty_blk(jt[i], y[i], bz[i], rk[i]);
+                v[1] += penalty_decrease_blk(j[i], jt[i], y[i], bz[i], rk[i]);
+            }
+        }
+        block_sum<2>(v, red[0]);
+        if (tid == 0) {
+            double g_t = 0.0, dg = 0.0;
+            const int np = n_parts(a, agent);
+            for (int ch = 0; ch < np; ++ch) {
+                if (!a.cost_from_decrease) g_t += a.part_cost[(size_t)agent * a.part_stride + ch];
+                dg += a.part_dcost[(size_t)agent * a.part_stride + ch];
+            }
+            if (a.cost_from_decrease) g_t = st.g - dg;
+            const double L_t = g_t + (double)v[0];
+            const double dL = dg + (double)v[1];  // L(J) - L(J')
+            st.g_t = g_t;
+            st.L_t = L_t;
+            const double ratio = (st.pred > 0.0 && isfinite(L_t) && isfinite(dL)) ? dL / st.pred : -INFINITY;
+            if (ratio < 0.25)
+                st.delta *= 0.25;
+            else if (ratio > 0.75 && (st.cg_stop == TCG_BOUNDARY || st.cg_stop == TCG_CURVATURE))
+                st.delta = fmin(2.0 * st.delta, st.delta_bar);
+            const int acc = ratio > RTR_ACCEPT;
+            if (acc) {
+                st.g = g_t;
+                st.L = L_t;
+                st.accepted += 1;
+            } else {
+                st.rejected += 1;
+            }
+            accept_s = acc;
+        }
+        __syncthreads();
+        fresh = accept_s != 0;
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            const int blk = tid + i * T;
+            if (blk >= KN) continue;
+            if (fresh) {
+                j[i] = jt[i];
+                st_blk(a.J + off, blk, j[i]);
+                gg[i] = sum_parts(a, agent, blk, KN);
+            } else {
+                gg[i] = ld_blk(a.gradg + off, blk);
+            }
+        }
+    } else {
+        float v[2] = {0.f, 0.f};  // penalty, ||J||^2
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            const int blk = tid + i * T;
+            if (blk >= KN) continue;
+            gg[i] = (mode == LM_BEGIN_FROM_PARTIALS || mode == LM_BEGIN_FROM_TRIAL) ? sum_parts(a, agent, blk, KN)
+                                                                                 : ld_blk(a.gradg + off, blk);
+            v[0] += penalty_blk(j[i], y[i], bz[i], rk[i]);
+            v[1] += dot8(j[i], j[i]);
+        }
+        block_sum<2>(v, red[0]);
+        if (tid == 0) {
+            if (mode == LM_BEGIN_FROM_PARTIALS) {
+                double g = 0.0;
+                for (int ch = 0; ch < n_parts(a, agent); ++ch) g += a.part_cost[(size_t)agent * a.part_stride + ch];
+                st.g = g;
+            } else if (mode == LM_BEGIN_FROM_TRIAL) {
+                st.g = 0.0;  // costs of this sub-problem are tracked relative to its start
+            }
+            st.L = st.g + (double)v[0];
+            st.delta_bar = sqrt(2.0 * (double)v[1]);
+            st.delta = st.delta_bar / 8.0;
+        }
+        fresh = mode == LM_BEGIN_FROM_PARTIALS || mode == LM_BEGIN_FROM_TRIAL;
+    }
+    if (fresh) {
+        project_out_gauge<BPT>(j, gg, K, N, sm, Asol);
+#pragma unroll
+        for (int i = 0; i < BPT; ++i) {
+            const int blk = tid + i * T;
+            if (blk < KN) st_blk(a.gradg + off, blk, gg[i]);
+        }
+    }
+    float rr[1] = {0.f};
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int blk = tid + i * T;
+        if (blk >= KN) continue;
+        Blk gr, r;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            gr.v[e] = gg[i].v[e] + 0.5f * y[i].v[e] + 0.5f * rk[i] * (j[i].v[e] - bz[i].v[e]);
+            r.v[e] = -gr.v[e];
+        }
+        st_blk(a.grad + off, blk, gr);
+        st_blk(a.r + off, blk, r);
+        st_blk(a.p + off, blk, r);
+        st_blk(a.x + off, blk, zero_blk());
+        rr[0] += dot8(r, r);
+    }
+    block_sum<1>(rr, red[2]);
+    if (tid == 0) {
+        const double h = 2.0 * (double)rr[0];
+        st.rz = h;
+        st.r0sq = h;
+        st.ee = 0.0;
+        st.cg_stop = (h > 0.0) ? TCG_RUNNING : TCG_RESIDUAL;
+    }
+}
+
 // calib_eval: L, g and grad L at a given J (sweep already ran on J), without touching the state.
 __global__ void __launch_bounds__(256) k_eval_output(const LMArgs a, float* grad_out, double* L_out, double* g_out) {
     __shared__ double red[32];
@@ -678,16 +956,32 @@ cudaError_t cg_go(const LMArgs& a, bool last, int threads, cudaStream_t s) {
     k_cg_step<BPT><<<a.A, threads, 0, s>>>(a, last ? 1 : 0);
     return cudaGetLastError();
 }
+template <int BPT>
+cudaError_t rtr_eval_go(const LMArgs& a, int mode, int threads, cudaStream_t s) {
+    const size_t smem = (size_t)a.K * a.N * GT * sizeof(float);
+    k_rtr_eval<BPT><<<a.A, threads, smem, s>>>(a, mode);
+    return cudaGetLastError();
+}
+template <int BPT>
+cudaError_t tcg_go(const LMArgs& a, bool last, int threads, cudaStream_t s) {
+    k_tcg_step<BPT><<<a.A, threads, 0, s>>>(a, last ? 1 : 0);
+    return cudaGetLastError();
+}
 
 }  // namespace
 
 cudaError_t prepare_lm_kernels() {
     const int smem = MAX_K * MAX_N * GT * (int)sizeof(float) > 200 * 1024 ? 200 * 1024 : MAX_K * MAX_N * GT * (int)sizeof(float);
+    const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_lm_eval<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_lm_eval<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(k_lm_eval<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_lm_eval<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if ((e = cudaFuncSetAttribute(k_lm_eval<1>, attr, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_lm_eval<2>, attr, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_lm_eval<4>, attr, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_lm_eval<8>, attr, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_rtr_eval<1>, attr, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_rtr_eval<2>, attr, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_rtr_eval<4>, attr, smem)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_rtr_eval<8>, attr, smem);
 }
 
 cudaError_t launch_lm_eval(const LMArgs& a, int mode, cudaStream_t s) {
@@ -708,6 +1002,27 @@ cudaError_t launch_cg_step(const LMArgs& a, bool last, cudaStream_t s) {
         case 2: return cg_go<2>(a, last, sh.threads, s);
         case 4: return cg_go<4>(a, last, sh.threads, s);
         case 8: return cg_go<8>(a, last, sh.threads, s);
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+cudaError_t launch_rtr_eval(const LMArgs& a, int mode, cudaStream_t s) {
+    const LMShape sh = lm_shape(a.K * a.N);
+    if ((size_t)a.K * a.N * GT * sizeof(float) > 200 * 1024) return cudaErrorInvalidConfiguration;
+    switch (sh.bpt) {
+        case 1: return rtr_eval_go<1>(a, mode, sh.threads, s);
+        case 2: return rtr_eval_go<2>(a, mode, sh.threads, s);
+        case 4: return rtr_eval_go<4>(a, mode, sh.threads, s);
+        case 8: return rtr_eval_go<8>(a, mode, sh.threads, s);
+        default: return cudaErrorInvalidConfiguration;
+    }
+}
+cudaError_t launch_tcg_step(const LMArgs& a, bool last, cudaStream_t s) {
+    const LMShape sh = lm_shape(a.K * a.N);
+    switch (sh.bpt) {
+        case 1: return tcg_go<1>(a, last, sh.threads, s);
+        case 2: return tcg_go<2>(a, last, sh.threads, s);
+        case 4: return tcg_go<4>(a, last, sh.threads, s);
+        case 8: return tcg_go<8>(a, last, sh.threads, s);
         default: return cudaErrorInvalidConfiguration;
     }
 }

@@ -30,8 +30,10 @@ Array conventions (all float64 / complex128):
 """
 from __future__ import annotations
 
+import concurrent.futures
 import dataclasses
 import math
+import os
 from typing import Sequence
 
 import numpy as np
@@ -257,8 +259,10 @@ def simulate_visibilities(Jt: np.ndarray, C: np.ndarray, pq: np.ndarray) -> np.n
 def make_problem(spec: ProblemSpec | str, seed: int | None = None, *, I: int | None = None,
                  P: int | None = None, N: int | None = None, K: int | None = None,
                  T: int | Sequence[int] | None = None, flag_max: float | None = None,
-                 noise: bool = True, dtype=complex) -> dict:
-    """Build a seeded problem. Keyword overrides shrink or reshape a named spec."""
+                 noise: bool = True, dtype=complex, coherencies: bool = True) -> dict:
+    """Build a seeded problem. Keyword overrides shrink or reshape a named spec.
+    coherencies=False drops the simulated coherencies from the result (C is None) for callers
+    that predict them from uvw and sky; every other array is unchanged."""
     if isinstance(spec, str):
         spec = SPECS[spec]
     kw = {}
@@ -308,9 +312,7 @@ def make_problem(spec: ProblemSpec | str, seed: int | None = None, *, I: int | N
         sky_bg[0, :, 1] = np.sin(rng.uniform(-half, half, spec.n_bg))
         sky_bg[0, :, 2] = rng.uniform(0.0, spec.bg_flux_max, spec.n_bg)
 
-    Cs, Vs = [], []
-    sig, cnt = 0.0, 0
-    for a in range(A):
+    def agent(a):  # deterministic (no random draws): safe to run agents concurrently
         iv, fi = divmod(a, P)
         Ta = int(T_agent[a])
         C = simulate_coherencies(uvw[iv, :Ta], sky, float(freqs[fi]), pq)
@@ -321,10 +323,23 @@ def make_problem(spec: ProblemSpec | str, seed: int | None = None, *, I: int | N
         if sky_bg is not None:  # uncorrupted: c_bg I_2
             cb = simulate_coherencies(uvw[iv, :Ta], sky_bg, float(freqs[fi]), pq)[:, :, 0]
             V = V + cb[:, :, None, None] * np.eye(2)
-        sig += float(np.sum(np.abs(V[flags[a] == 0]) ** 2))
-        cnt += int(np.sum(flags[a] == 0)) * Ta * 4
-        Cs.append(C.astype(dtype, copy=False))
-        Vs.append(V.astype(dtype, copy=False))
+        s_a = float(np.sum(np.abs(V[flags[a] == 0]) ** 2))
+        C_out = C.astype(dtype, copy=False) if coherencies else None
+        return C_out, V.astype(dtype, copy=False), s_a, int(np.sum(flags[a] == 0)) * Ta * 4
+
+    workers = min(A, os.cpu_count() or 1) if A >= 64 else 1
+    if workers > 1:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=workers) as ex:
+            per_agent = list(ex.map(agent, range(A)))
+    else:
+        per_agent = [agent(a) for a in range(A)]
+    Cs = [r[0] for r in per_agent] if coherencies else None
+    Vs = [r[1] for r in per_agent]
+    sig, cnt = 0.0, 0
+    for r in per_agent:  # summed in agent order: the same noise level however the agents ran
+        sig += r[2]
+        cnt += r[3]
+    del per_agent
     # Noise: total noise power = total signal power / SNR over all unflagged data
     # (equal variance in real and imaginary parts, Section 2 and Section 4).
     sigma = math.sqrt(sig / cnt / (2.0 * spec.snr)) if (noise and cnt) else 0.0

@@ -74,7 +74,22 @@ CASES = {
     "n8_t700": lambda: make_problem("tiny_n8_k1", N=8, P=3, T=700, seed=23),
     # more than 64 stations (a 96-thread Hessian sweep, 3 warps) and four directions
     "n66_k4": lambda: make_problem("adjoint_n16_k3", N=66, K=4, P=4, I=1, T=2, flag_max=0.05, seed=24),
+    # the largest register buckets of the statistics sweeps (K = 12 and K = 16)
+    "n12_k12": lambda: make_problem("adjoint_n16_k3", N=12, K=12, P=4, I=1, T=2, flag_max=0.1, seed=25),
+    "n10_k16": lambda: make_problem("adjoint_n16_k3", N=10, K=16, P=4, I=1, T=2, seed=26),
+    # the largest station count (8128 baselines; 256-thread trial sweep, 128-thread Hessian sweep)
+    "n128_k2": lambda: make_problem("adjoint_n16_k3", N=128, K=2, P=4, I=1, T=1, seed=27),
+    # the paper's 47-station array with 16 directions: beyond the statistics sweeps' shared memory,
+    # so only the direct formulation takes it
+    "n47_k16": lambda: make_problem("adjoint_n16_k3", N=47, K=16, P=4, I=1, T=2, seed=28),
 }
+DIRECT_ONLY = {"n47_k16"}
+
+
+def form_kw(case):
+    """Options of a case's context for the single-pass tests (the direct form where the statistics
+    sweeps do not take the shape)."""
+    return {"formulation": capi.CALIB_FORM_DIRECT} if case in DIRECT_ONLY else {}
 
 
 def random_state(prob, seed):
@@ -90,7 +105,7 @@ def random_state(prob, seed):
 def test_eval_matches_oracle(lib, case):
     prob = CASES[case]()
     pr = rounded(prob)
-    cal = calibrator(lib, prob)
+    cal = calibrator(lib, prob, **form_kw(case))
     J, Z, Y = random_state(prob, 11)
     cal.set_consensus(Z, Y)
     L, g, grad = cal.eval(J)
@@ -112,7 +127,7 @@ def test_eval_matches_oracle(lib, case):
 def test_hessvec_matches_oracle(lib, case):
     prob = CASES[case]()
     pr = rounded(prob)
-    cal = calibrator(lib, prob)
+    cal = calibrator(lib, prob, **form_kw(case))
     J, _, _ = random_state(prob, 12)
     rng = np.random.default_rng(13)
     eta = cn(rng, *J.shape).astype(np.complex64)
@@ -194,6 +209,65 @@ def test_predict_matches_oracle(lib, case):
         assert np.all(blk[~keep] == 0)
 
 
+def test_predict_full_size_lofar_sample(lib):
+    """calib_predict on the whole LOFAR-shaped batch (320 agents, 1891 baselines, 10 samples, 5
+    clusters of 20 sources): agents at both band edges and in the middle, of the first and last
+    intervals, every baseline (the longest reach about 80 km, thousands of turns), element by
+    element against the float64 oracle. The turns are formed in float64 and reduced to [-1/2, 1/2)
+    before float32 sincospi, so each source's term is off by a few float32 ulps of its flux; the
+    bound 2e-5 of the cluster's summed flux covers the 20-term sum."""
+    prob = make_problem("lofar_n62_k5")
+    cal = calibrator(lib, prob)
+    cal.predict(prob["uvw"], prob["sky"], prob["f0"])
+    got = cal.coherencies()
+    P, B, K, T = prob["P"], prob["B"], prob["K"], 10
+    longest = np.argmax(np.linalg.norm(prob["uvw"][0, 0, prob["pq"][:, 0]] - prob["uvw"][0, 0, prob["pq"][:, 1]], axis=1))
+    for a in (0, P // 2, P - 1, prob["A"] - P, prob["A"] - 1):
+        iv, f = divmod(a, P)
+        blk = got[a * B * T * K: (a + 1) * B * T * K].reshape(B, T, K)
+        ref = O.predict_coherencies(prob["uvw"][iv], prob["sky"], prob["freqs"][f], prob["f0"], prob["pq"])
+        flux = (prob["sky"][..., 2] * (prob["freqs"][f] / prob["f0"]) ** prob["sky"][..., 3]).sum(-1)
+        err = np.abs(blk - ref).max(axis=(0, 1))
+        assert np.all(err <= 2e-5 * flux), (a, err / flux)
+        assert np.abs(blk[longest] - ref[longest]).max() <= 2e-5 * flux.max()
+    cal.close()
+
+
+def test_statistics_form_rejects_shapes_beyond_its_shared_memory(lib):
+    """47 stations x 16 directions need more shared memory than the statistics sweeps have:
+    calib_init refuses that formulation with CALIB_EINVAL and names the direct one."""
+    prob = CASES["n47_k16"]()
+    with pytest.raises(capi.CalibError) as e:
+        Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
+                   n_intervals=prob["I"], samples=prob["T"], formulation=capi.CALIB_FORM_STATISTICS)
+    assert e.value.code == capi.CALIB_EINVAL and "CALIB_FORM_DIRECT" in str(e.value)
+
+
+def test_full_size_uneven_first_jupdate_sample(lib):
+    """The batched uneven workload at full size (2560 agents: 256 subbands x 10 intervals, 62
+    stations, K = 10, 5/10/20 samples per subband, 0-15 % of baselines flagged) in its own launch
+    configuration (autotuned statistics sweeps). From the cold start (Z = Y = 0) the first J-update
+    of every agent is independent of the others and the gauge projection leaves g unchanged, so the
+    oracle's LM J-update of single agents gives their g after one C-ADMM iteration."""
+    prob = make_problem("uneven_n62_k10")
+    cal = calibrator(lib, prob)
+    cal.iterate(1)
+    _, g = cal.agent_objective()
+    cal.close()
+    T, flags = prob["T"], prob["flags"]
+    P = prob["P"]
+    picks = [int(np.argmax(T[:P] == t)) for t in (5, 10, 20)]
+    picks.append(int(np.argmax(flags[:P].mean(axis=1))))
+    pr_rho = prob["rho"]
+    for a in picks:
+        keep = flags[a] == 0
+        V, C, pq = c64(prob["V"][a][keep]), c64(prob["C"][a][keep]), prob["pq"][keep]
+        J0 = np.broadcast_to(np.eye(2, dtype=complex), (prob["K"], prob["N"], 2, 2)).copy()
+        zero = np.zeros_like(J0)
+        J = O.lm_jupdate(J0, V, C, pq, zero, zero, pr_rho, 10, 4)
+        assert g[a] == pytest.approx(O.data_cost(J, V, C, pq), rel=REL_ADMM), (a, int(T[a]), float(flags[a].mean()))
+
+
 def run_both(lib, prob, n_iter, n_lm=10, n_cg=4, form="statistics"):
     cal = calibrator(lib, prob, n_lm=n_lm, n_cg=n_cg, formulation=FORMS[form])
     hist = cal.iterate(n_iter)
@@ -201,9 +275,12 @@ def run_both(lib, prob, n_iter, n_lm=10, n_cg=4, form="statistics"):
     return cal, hist, ref
 
 
-@pytest.mark.parametrize("form", sorted(FORMS))
-@pytest.mark.parametrize("case", ["tiny_n8_k1", "ragged_n13_k3", "n2_single_baseline", "n10_k10_flagged", "n9_k7",
-                                  "n8_t700", "n66_k4"])
+HISTORY_CASES = ["tiny_n8_k1", "ragged_n13_k3", "n2_single_baseline", "n10_k10_flagged", "n9_k7", "n8_t700", "n66_k4",
+                 "n12_k12", "n10_k16", "n128_k2", "n47_k16"]
+
+
+@pytest.mark.parametrize("case,form", [(c, f) for c in HISTORY_CASES for f in sorted(FORMS)
+                                       if not (c in DIRECT_ONLY and f == "statistics")])
 def test_admm_history_matches_oracle(lib, case, form):
     prob = CASES[case]()
     n_iter = 10 if case == "tiny_n8_k1" else 4

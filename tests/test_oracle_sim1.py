@@ -19,7 +19,7 @@ import pytest
 
 from oracle import admm as O
 from oracle import rtr as R
-from paper_1502_00858_gb300 import sim1
+from experiments import sim1
 from synth import make_problem
 
 

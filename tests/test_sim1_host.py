@@ -8,7 +8,7 @@ import math
 import numpy as np
 import pytest
 
-from paper_1502_00858_gb300 import sim1
+from experiments import sim1
 from synth import make_problem
 from synth.lofar import simulate_visibilities
 
