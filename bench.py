@@ -46,12 +46,11 @@ UNIT = "vis*dir*iter/s"
 # DRAM traffic per launch of each sweep kernel from one ncu capture; valid only for the kernel
 # source it was taken on (sha256 prefix of the kernel's .cu file), else reported as null.
 NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum of one full capture each (summaries in profiles/)
-    ("stats_hessvec", "146072fb36a2"): 82.55e6,
     ("stats_pass", "532c6d147726"): 595.5e6,
     ("residual", "532c6d147726"): 615.2e6,
 }
-KERNEL_SOURCE = {"sweep_residual": "sweep.cu", "sweep_hessvec": "sweep.cu",
-                 "stats_hessvec": "ss.cu", "stats_trial": "ss.cu", "stats_pass": "data.cu", "residual": "data.cu"}
+KERNEL_SOURCE = {"sweep_residual": "sweep.cu", "sweep_hessvec": "sweep.cu", "stats_hessvec": "ss_hessvec.cu",
+                 "stats_trial": "ss.cu", "stats_pass": "data.cu", "residual": "data.cu"}
 # The sufficient-statistics passes do 13-17 real flops per algorithmic byte at K=5, above the FP32
 # ridge (~12 flop/B): their roofline is the FP32 pipe. The direct passes are below it (HBM).
 ALU_BOUND = {"stats_hessvec", "stats_trial"}

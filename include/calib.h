@@ -19,7 +19,9 @@
  *
  * Symbols: N stations, B baselines (pairs p<q), K directions, P frequencies (agents
  * per interval), M basis terms (the paper calls this F), I solution intervals,
- * A = I*P agents (agent a = interval*P + frequency index), T_a samples of agent a.
+ * A = I*P agents (agent a = interval*P + frequency index), T_a samples of agent a,
+ * G frequency groups per interval (calib_options.freq_groups, default 1): I*G consensus
+ * problems, problem (interval, g) holding the agents of frequency indices g, g+G, ...
  *
  * Conventions for every entry point:
  *  - Return value: CALIB_OK (0) or a negative CALIB_E* code; calib_last_error() then
@@ -97,6 +99,13 @@ typedef struct {
                                           the (agent, diagonal) items; 0 = automatic */
     int jupdate;                       /* CALIB_JUPDATE_LM (default), CALIB_JUPDATE_RTR or CALIB_JUPDATE_SAGE */
     int n_sage;                        /* SAGE sweeps per J-update (default 1; CALIB_JUPDATE_SAGE only) */
+    int freq_groups;                   /* G >= 1 (default 1), dividing P: frequency multiplexing. With more
+                                          frequencies than agents per consensus problem (Section 3), each
+                                          interval's P frequencies form G interleaved subsets - subset g is
+                                          the frequency indices g, g+G, g+2G, ... (each spans the band) -
+                                          and every subset is its own C-ADMM problem of P/G agents with its
+                                          own Z (the paper repeats the selection sequentially; here the
+                                          I*G problems run in the same batch). Needs P/G >= M. */
 } calib_options;
 
 /* One record per C-ADMM iteration (Section 4 definitions, summed/averaged over all intervals):
@@ -162,7 +171,7 @@ int calib_reset(calib_ctx* ctx);
  * from a previous solution interval (Section 3, initialisation). Z and Y are unchanged. */
 int calib_set_initial(calib_ctx* ctx, const void* J0, int ptr_kind);
 
-/* Set the consensus state: Z c128 [I][K][M][N][2][2] and Y c64 [A][K][N][2][2] (either may
+/* Set the consensus state: Z c128 [I][G][K][M][N][2][2] and Y c64 [A][K][N][2][2] (either may
  * be NULL = zero). B_i Z is recomputed. A state set this way is warm: no gauge projection.
  * With calib_get_solutions this is checkpoint and resume. */
 int calib_set_consensus(calib_ctx* ctx, const void* Z, const void* Y, int ptr_kind);
@@ -172,7 +181,7 @@ int calib_set_consensus(calib_ctx* ctx, const void* Z, const void* Y, int ptr_ki
  * in-kernel wait gave up. */
 int calib_admm_iter(calib_ctx* ctx, int n_iters, calib_stats* hist);
 
-/* Copy out J c64 [A][K][N][2][2], Z c128 [I][K][M][N][2][2], Y c64 [A][K][N][2][2].
+/* Copy out J c64 [A][K][N][2][2], Z c128 [I][G][K][M][N][2][2], Y c64 [A][K][N][2][2].
  * Any pointer may be NULL. */
 int calib_get_solutions(calib_ctx* ctx, void* J, void* Z, void* Y, int ptr_kind);
 
@@ -261,7 +270,7 @@ void calib_mlp_destroy(calib_mlp* mlp);
  * following interval. */
 int calib_get_features(calib_ctx* ctx, float* X, int ptr_kind);
 /* Warm start of the next calib_admm_iter from the previous interval's solution J_prev c64 [A][K][N][2][2]
- * and consensus Z_prev c128 [I][K][M][N][2][2]: Z = Z_prev, Y = 0 (warm: no gauge projection), and per
+ * and consensus Z_prev c128 [I][G][K][M][N][2][2]: Z = Z_prev, Y = 0 (warm: no gauge projection), and per
  * agent J = J_prev + network(J_prev, B_f Z_prev, f) where that gives the lower L_i, else J = J_prev
  * (mlp NULL: always J_prev). chose [A] (may be NULL) receives 1 where the network's start was kept. */
 int calib_warm_start(calib_ctx* ctx, calib_mlp* mlp, const void* J_prev, const void* Z_prev, int* chose, int ptr_kind);

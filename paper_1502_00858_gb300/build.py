@@ -20,7 +20,7 @@ LIB = os.path.join(PKG, "libcalib.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
-SOURCES = ["sweep.cu", "ss.cu", "lm.cu", "consensus.cu", "data.cu", "capi.cu", "noalloc.cu", "mlp.cu", "sage.cu"]
+SOURCES = ["sweep.cu", "ss.cu", "lm.cu", "consensus.cu", "data.cu", "capi.cu", "noalloc.cu", "mlp.cu", "sage.cu", "ss_hessvec.cu"]
 
 
 def nvcc() -> str:

@@ -12,19 +12,20 @@ class Calibrator:
 
     def __init__(self, N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, samples=1, n_lm=10, n_cg=4,
                  chunk_diagonals=0, cuda_stream=None, formulation=capi.CALIB_FORM_STATISTICS, ctas_per_sm=0,
-                 jupdate=capi.CALIB_JUPDATE_LM, n_sage=1):
+                 jupdate=capi.CALIB_JUPDATE_LM, n_sage=1, freq_groups=1):
         spa = None if np.isscalar(samples) else np.asarray(samples, dtype=np.int32)
         self.N, self.K, self.P = int(N), int(K), len(freqs_hz)
         self.M = int(np.asarray(basis).shape[1])
         self.I = int(n_intervals)
         self.A = self.I * self.P
+        self.G = int(freq_groups)
         self.B = int(np.asarray(pq).shape[0])
         self.T = spa if spa is not None else np.full(self.A, int(samples), dtype=np.int32)
         self.ctx = capi.calib_init(N, pq, K, freqs_hz, basis, rho, n_intervals=n_intervals,
                                    n_samples=int(samples) if spa is None else 1, samples_per_agent=spa,
                                    n_lm=n_lm, n_cg=n_cg, chunk_diagonals=chunk_diagonals, cuda_stream=cuda_stream,
                                    formulation=formulation, ctas_per_sm=ctas_per_sm, jupdate=jupdate,
-                                   n_sage=n_sage)
+                                   n_sage=n_sage, freq_groups=freq_groups)
 
     # shapes of the public arrays
     @property
@@ -33,7 +34,8 @@ class Calibrator:
 
     @property
     def z_shape(self):
-        return (self.I, self.K, self.M, self.N, 2, 2)
+        """Z per consensus problem (interval * G + frequency group), [I*G][K][M][N][2][2]."""
+        return (self.I * self.G, self.K, self.M, self.N, 2, 2)
 
     def set_data(self, vis, coh=None, flags=None):
         capi.calib_set_data(self.ctx, vis, coh, flags)

@@ -33,7 +33,8 @@ EXPORTED = [
 class CalibOptions(C.Structure):
     _fields_ = [("n_intervals", C.c_int), ("n_samples", C.c_int), ("samples_per_agent", C.POINTER(C.c_int32)),
                 ("n_lm", C.c_int), ("n_cg", C.c_int), ("chunk_diagonals", C.c_int), ("cuda_stream", C.c_void_p),
-                ("formulation", C.c_int), ("ctas_per_sm", C.c_int), ("jupdate", C.c_int), ("n_sage", C.c_int)]
+                ("formulation", C.c_int), ("ctas_per_sm", C.c_int), ("jupdate", C.c_int), ("n_sage", C.c_int),
+                ("freq_groups", C.c_int)]
 
 
 class CalibStats(C.Structure):
@@ -140,7 +141,7 @@ def calib_default_options() -> CalibOptions:
 
 def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, samples_per_agent=None,
                n_lm=10, n_cg=4, chunk_diagonals=0, cuda_stream=None, formulation=CALIB_FORM_STATISTICS,
-               ctas_per_sm=0, jupdate=CALIB_JUPDATE_LM, n_sage=1):
+               ctas_per_sm=0, jupdate=CALIB_JUPDATE_LM, n_sage=1, freq_groups=1):
     lib = load()
     pq_a = np.ascontiguousarray(pq, dtype=np.int32)
     fr = np.ascontiguousarray(freqs_hz, dtype=np.float64)
@@ -153,6 +154,7 @@ def calib_init(N, pq, K, freqs_hz, basis, rho, *, n_intervals=1, n_samples=1, sa
     opt.ctas_per_sm = ctas_per_sm
     opt.jupdate = jupdate
     opt.n_sage = n_sage
+    opt.freq_groups = freq_groups
     spa = None
     if samples_per_agent is not None:
         spa = np.ascontiguousarray(samples_per_agent, dtype=np.int32)

@@ -118,7 +118,11 @@ struct ConsArgs {
     double* dual2;          // [I][K][8] per-CTA shares of ||Z_k^{n+1} - Z_k^n||^2
     double* stats;          // [max_iters][4]
     int* iter_counter;
-    int A, I, P, M, N, K, max_iters;
+    // Consensus problems: each of the I intervals' P frequencies splits into G interleaved groups
+    // (group g = frequency indices g, g + G, ...; G = 1: one problem per interval), each its own
+    // C-ADMM problem of P / G agents (frequency multiplexing, Section 3). Problem pb = iv * G + g;
+    // its j-th agent is iv * P + g + G * j. Z and Zprev are [I * G][K][M][N][8]; Pinv is [G][M][M].
+    int A, I, P, M, N, K, max_iters, G;
 };
 
 // ---- launchers (sweep.cu)
@@ -216,6 +220,9 @@ cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, int grid, cudaStream_
 size_t ss_sweep_smem_bytes(int N, int K, bool hessvec, int* stage_bytes);
 int ss_sweep_threads(int N);
 cudaError_t prepare_ss_kernels();
+// the one-thread-per-slot Hessian pass (K <= 5, ss_hessvec.cu)
+cudaError_t prepare_ss_hessvec_kernels();
+cudaError_t launch_ss_hessvec1(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s);
 
 // One-time kernel attribute set-up (dynamic shared memory limits); call before any capture.
 cudaError_t prepare_sweep_kernels();

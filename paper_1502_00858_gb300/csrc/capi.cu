@@ -78,6 +78,7 @@ struct TuneEntry {
 struct calib_ctx {
     int dev = 0;
     int N = 0, B = 0, K = 0, P = 0, M = 0, I = 0, A = 0, D = 0;
+    int G = 1;  // frequency groups per interval: I * G consensus problems of P / G agents
     int n_lm = 10, n_cg = 4, chunk_diags = 1, n_chunks = 1, slots_max = 4;
     int jupdate = 0;               // CALIB_JUPDATE_LM, CALIB_JUPDATE_RTR or CALIB_JUPDATE_SAGE
     int n_sage = 1;                // SAGE sweeps over the directions per J-update
@@ -333,6 +334,7 @@ ConsArgs cons_args(calib_ctx* c) {
     a.A = c->A;
     a.I = c->I;
     a.P = c->P;
+    a.G = c->G;
     a.M = c->M;
     a.N = c->N;
     a.K = c->K;
@@ -811,6 +813,7 @@ void calib_default_options(calib_options* opt) {
     opt->ctas_per_sm = 0;
     opt->jupdate = CALIB_JUPDATE_LM;
     opt->n_sage = 1;
+    opt->freq_groups = 1;
 }
 
 int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* pq, int n_dirs, int n_freqs,
@@ -828,7 +831,11 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     if (P < 1) return fail(CALIB_EINVAL, "n_freqs must be >= 1");
     if (M < 1 || M > MAX_M) return fail(CALIB_EINVAL, "n_basis must be in [1, 16]");
     if (!pq || !freqs_hz || !basis || !rho) return fail(CALIB_EINVAL, "pq, freqs_hz, basis and rho are required");
-    if (P < M) return fail(CALIB_ERANK, "need at least as many frequencies as basis terms (P >= M)");
+    const int G = opt.freq_groups < 1 ? 1 : opt.freq_groups;
+    if (P % G != 0) return fail(CALIB_EINVAL, "freq_groups must divide n_freqs");
+    if (P / G < M)
+        return fail(CALIB_ERANK, "need at least as many frequencies as basis terms in every consensus problem (P >= M; "
+                                 "P/G >= M with frequency groups)");
     if (opt.n_intervals < 1) return fail(CALIB_EINVAL, "n_intervals must be >= 1");
     if (opt.n_lm < 1 || opt.n_cg < 1) return fail(CALIB_EINVAL, "n_lm and n_cg must be >= 1");
     if (opt.formulation != CALIB_FORM_STATISTICS && opt.formulation != CALIB_FORM_DIRECT)
@@ -855,12 +862,17 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
         T[a] = opt.samples_per_agent ? opt.samples_per_agent[a] : opt.n_samples;
         if (T[a] < 1) return fail(CALIB_EINVAL, "every agent needs at least one sample");
     }
+    // (sum_i b_i b_i^T)^-1 of every frequency group (its interleaved rows g, g + G, ...)
     std::vector<double> Pinv;
-    if (!invert_gram(std::vector<double>(basis, basis + (size_t)P * M), P, M, Pinv))
-        return fail(CALIB_ERANK, "sum_i b_i b_i^T is singular");
+    for (int g = 0; g < G; ++g) {
+        std::vector<double> rows, inv;
+        for (int f = g; f < P; f += G) rows.insert(rows.end(), basis + (size_t)f * M, basis + (size_t)(f + 1) * M);
+        if (!invert_gram(rows, P / G, M, inv)) return fail(CALIB_ERANK, "sum_i b_i b_i^T is singular");
+        Pinv.insert(Pinv.end(), inv.begin(), inv.end());
+    }
 
     calib_ctx* c = new calib_ctx();
-    c->N = N; c->B = B; c->K = K; c->P = P; c->M = M; c->I = opt.n_intervals; c->A = A;
+    c->N = N; c->B = B; c->K = K; c->P = P; c->M = M; c->I = opt.n_intervals; c->A = A; c->G = G;
     c->D = N / 2;
     c->n_lm = opt.n_lm;
     c->n_cg = opt.n_cg;
@@ -927,12 +939,12 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     okm = okm && dalloc(&c->part, (size_t)A * c->D * K * N * 8) == cudaSuccess;
     okm = okm && dalloc(&c->part_cost, (size_t)A * c->D) == cudaSuccess;
     okm = okm && dalloc(&c->part_dcost, (size_t)A * c->D) == cudaSuccess;
-    const size_t zs = (size_t)c->I * K * M * N * 8;
+    const size_t zs = (size_t)c->I * c->G * K * M * N * 8;
     okm = okm && dalloc(&c->Z, zs) == cudaSuccess && dalloc(&c->Zprev, zs) == cudaSuccess;
-    okm = okm && dalloc(&c->basis_d, (size_t)P * M) == cudaSuccess && dalloc(&c->Pinv_d, (size_t)M * M) == cudaSuccess;
+    okm = okm && dalloc(&c->basis_d, (size_t)P * M) == cudaSuccess && dalloc(&c->Pinv_d, (size_t)c->G * M * M) == cudaSuccess;
     okm = okm && dalloc(&c->freqs_d, (size_t)P) == cudaSuccess && dalloc(&c->rho_d, (size_t)K) == cudaSuccess;
     okm = okm && dalloc(&c->st, (size_t)A) == cudaSuccess && dalloc(&c->prim, (size_t)A * K) == cudaSuccess;
-    okm = okm && dalloc(&c->dual2, (size_t)c->I * K * 8) == cudaSuccess;
+    okm = okm && dalloc(&c->dual2, (size_t)c->I * c->G * K * 8) == cudaSuccess;
     okm = okm && dalloc(&c->iter_counter, 1) == cudaSuccess && dalloc(&c->status, 1) == cudaSuccess;
     okm = okm && dalloc(&c->evL, (size_t)A) == cudaSuccess && dalloc(&c->evG, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess && dalloc(&c->part_hv.pn, (size_t)A) == cudaSuccess &&
@@ -978,7 +990,7 @@ int calib_reset(calib_ctx* c) {
     CK(launch_identity(c->J, (long long)c->A * c->K * c->N, c->stream));
     CK(cudaMemsetAsync(c->Y, 0, vec * sizeof(float), c->stream));
     CK(cudaMemsetAsync(c->BZ, 0, vec * sizeof(float), c->stream));
-    const size_t zs = (size_t)c->I * c->K * c->M * c->N * 8;
+    const size_t zs = (size_t)c->I * c->G * c->K * c->M * c->N * 8;
     CK(cudaMemsetAsync(c->Z, 0, zs * sizeof(double), c->stream));
     CK(cudaMemsetAsync(c->Zprev, 0, zs * sizeof(double), c->stream));
     c->launches += 1;
@@ -1181,7 +1193,7 @@ int calib_set_consensus(calib_ctx* c, const void* Zin, const void* Yin, int ptr_
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
     const cudaMemcpyKind kind = ptr_kind == 1 ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-    const size_t zs = (size_t)c->I * c->K * c->M * c->N * 8 * sizeof(double);
+    const size_t zs = (size_t)c->I * c->G * c->K * c->M * c->N * 8 * sizeof(double);
     const size_t ys = (size_t)c->A * c->K * c->N * 8 * sizeof(float);
     if (Zin) CK(cudaMemcpyAsync(c->Z, Zin, zs, kind, c->stream));
     else CK(cudaMemsetAsync(c->Z, 0, zs, c->stream));
@@ -1289,7 +1301,7 @@ namespace {
 struct StateHeader {
     char magic[8];          // "CALIBST1"
     int32_t version;        // 1
-    int32_t N, B, K, P, M, I, A, formulation;
+    int32_t N, B, K, P, M, I, A, formulation, G;
     int32_t cold;           // the next iteration applies the first-iteration gauge projection
     int32_t need_eval;      // the next iteration starts with a residual sweep at J
     int64_t iters_done;     // C-ADMM iterations since the last cold start or warm state
@@ -1314,7 +1326,7 @@ struct StatePart { void* dev; size_t bytes; };
 std::vector<StatePart> state_parts(calib_ctx* c) {
     const size_t vb = (size_t)c->A * c->K * c->N * 8 * sizeof(float);
     const size_t gb = (size_t)c->A * c->K * c->N * 4 * sizeof(float);
-    const size_t zb = (size_t)c->I * c->K * c->M * c->N * 8 * sizeof(double);
+    const size_t zb = (size_t)c->I * c->G * c->K * c->M * c->N * 8 * sizeof(double);
     return {{c->J, vb}, {c->Y, vb}, {c->BZ, vb}, {c->gradg, vb}, {c->Gm, gb},
             {c->Z, zb}, {c->Zprev, zb}, {c->st, (size_t)c->A * sizeof(AgentState)}};
 }
@@ -1345,6 +1357,7 @@ int calib_get_state(calib_ctx* c, void* buf, size_t* len) {
     h.version = 1;
     h.N = c->N; h.B = c->B; h.K = c->K; h.P = c->P; h.M = c->M; h.I = c->I; h.A = c->A;
     h.formulation = c->formulation;
+    h.G = c->G;
     h.cold = c->cold ? 1 : 0;
     h.need_eval = c->need_eval ? 1 : 0;
     h.iters_done = c->iters_done;
@@ -1371,7 +1384,7 @@ int calib_set_state(calib_ctx* c, const void* buf, size_t len) {
     if (std::memcmp(h.magic, "CALIBST1", 8) != 0 || h.version != 1)
         return fail(CALIB_EINVAL, "not a calibration state blob (magic or version)");
     if (h.N != c->N || h.B != c->B || h.K != c->K || h.P != c->P || h.M != c->M || h.I != c->I || h.A != c->A ||
-        h.formulation != c->formulation)
+        h.formulation != c->formulation || h.G != c->G)
         return fail(CALIB_EINVAL, "state blob was saved for another problem shape or formulation");
     if (h.pair_hash != layout_hash(c))
         return fail(CALIB_EINVAL, "state blob was saved for other station pairs, samples or flags");
@@ -1394,7 +1407,7 @@ int calib_get_solutions(calib_ctx* c, void* J, void* Zo, void* Yo, int ptr_kind)
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     if (!valid_kind(ptr_kind)) return fail(CALIB_EINVAL, "ptr_kind must be 0 (host) or 1 (device)");
     const size_t vb = (size_t)c->A * c->K * c->N * 8 * sizeof(float);
-    const size_t zb = (size_t)c->I * c->K * c->M * c->N * 8 * sizeof(double);
+    const size_t zb = (size_t)c->I * c->G * c->K * c->M * c->N * 8 * sizeof(double);
     int rc;
     if ((rc = copy_out(c, J, c->J, vb, ptr_kind))) return rc;
     if ((rc = copy_out(c, Zo, c->Z, zb, ptr_kind))) return rc;

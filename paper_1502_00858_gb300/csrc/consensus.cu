@@ -33,7 +33,7 @@ __device__ __forceinline__ C2 cadd(C2 a, C2 b) { return {a.r + b.r, a.i + b.i}; 
 
 // First C-ADMM iteration (Section 3, initialisation): rotate each agent's J_k by the unitary
 // polar factor U of M = J_k^H J_ref,k (the 2x2 Procrustes solution, min_U ||J_ref - J U||), the
-// reference being the agent at frequency index P/2 of the same interval. For 2x2 M with
+// reference being the middle agent (index P_g / 2) of the same consensus problem. For 2x2 M with
 // det M = |det M| e^{i theta}: U = (M + e^{i theta} adj(M)^H) / sqrt(||M||_F^2 + 2 |det M|).
 // The stored data gradient and Jacobi blocks are rotated with J (grad g(JU) = grad g(J) U,
 // G(JU) = U^H G U) since g is invariant under the common unitary.
@@ -42,7 +42,8 @@ __global__ void __launch_bounds__(CT) k_gauge(const ConsArgs a) {
     __shared__ C2 U[4];
     const int agent = blockIdx.x;
     const int iv = agent / a.P, f = agent - iv * a.P;
-    const int ref = iv * a.P + a.P / 2;
+    const int g = f % a.G, Pg = a.P / a.G;
+    const int ref = iv * a.P + g + a.G * (Pg / 2);
     if (agent == ref) return;
     const int N = a.N;
     for (int k = 0; k < a.K; ++k) {
@@ -123,23 +124,25 @@ constexpr int ZSLOTS = 8;  // CTAs per (interval, direction): 8N / ZT <= 8 for N
 
 __global__ void __launch_bounds__(ZT) k_zupdate(const ConsArgs a) {
     __shared__ double red[33];
-    const int ivk = blockIdx.x;
-    const int k = ivk % a.K, iv = ivk / a.K;
+    const int ivk = blockIdx.x;  // (consensus problem, direction)
+    const int k = ivk % a.K, pb = ivk / a.K;
+    const int iv = pb / a.G, g = pb - iv * a.G, Pg = a.P / a.G;
     const int j = blockIdx.y * ZT + threadIdx.x;  // (station, entry) = (j / 8, j % 8)
     const int NE = a.N * 8, M = a.M;
     const double rk = a.rho[k];
+    const double* Pinv = a.Pinv + (size_t)g * M * M;
     double dz2 = 0.0;
     if (j < NE) {
         double R[MAX_M];
 #pragma unroll
         for (int l = 0; l < MAX_M; ++l) R[l] = 0.0;
-        const size_t stride = (size_t)a.K * NE;  // next frequency, same direction
-        const size_t o0 = ((size_t)iv * a.P * a.K + k) * NE + j;
+        const size_t stride = (size_t)a.G * a.K * NE;  // next agent of the problem, same direction
+        const size_t o0 = (((size_t)iv * a.P + g) * a.K + k) * NE + j;
 #pragma unroll 4
-        for (int f = 0; f < a.P; ++f) {
-            const size_t o = o0 + (size_t)f * stride;
+        for (int jj = 0; jj < Pg; ++jj) {
+            const size_t o = o0 + (size_t)jj * stride;
             const double v = (double)__ldg(a.Y + o) + rk * (double)__ldg(a.J + o);
-            const double* bf = a.basis + (size_t)f * M;
+            const double* bf = a.basis + (size_t)(g + a.G * jj) * M;
 #pragma unroll
             for (int l = 0; l < MAX_M; ++l)
                 if (l < M) R[l] = fma(__ldg(bf + l), v, R[l]);
@@ -150,9 +153,9 @@ __global__ void __launch_bounds__(ZT) k_zupdate(const ConsArgs a) {
             double z = 0.0;
 #pragma unroll
             for (int m = 0; m < MAX_M; ++m)
-                if (m < M) z = fma(__ldg(a.Pinv + l * M + m), R[m], z);
+                if (m < M) z = fma(__ldg(Pinv + l * M + m), R[m], z);
             z /= rk;
-            const size_t zo = (((size_t)iv * a.K + k) * M + l) * NE + j;
+            const size_t zo = (((size_t)pb * a.K + k) * M + l) * NE + j;
             const double old = a.Z[zo];
             a.Zprev[zo] = old;
             a.Z[zo] = z;
@@ -173,6 +176,7 @@ __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) 
     extern __shared__ double dds[];  // [K][N] ||J - BZ||^2 per block
     const int agent = blockIdx.x;
     const int iv = agent / a.P, f = agent - iv * a.P;
+    const int pb = iv * a.G + f % a.G;  // the agent's consensus problem
     const int N = a.N, KN8 = a.K * N * 8, M = a.M;
     double bl[MAX_M];
 #pragma unroll
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) 
             const int k = i / (N * 8), pe = i - k * N * 8;  // pe = station * 8 + entry
             const double rk = a.rho[k];
             const size_t o = (size_t)agent * KN8 + i;
-            const double* z = a.Z + ((size_t)iv * a.K + k) * M * N * 8 + pe;  // Z[iv][k][l][p][e] at l = 0
+            const double* z = a.Z + ((size_t)pb * a.K + k) * M * N * 8 + pe;  // Z[pb][k][l][p][e] at l = 0
             double bz = 0.0;
 #pragma unroll
             for (int l = 0; l < MAX_M; ++l)
@@ -218,7 +222,7 @@ __global__ void __launch_bounds__(CT) k_stats(const ConsArgs a) {
     double prim = 0.0, dual = 0.0, obj = 0.0, g = 0.0;
     for (int i = threadIdx.x; i < a.A * a.K; i += blockDim.x) prim += a.prim[i];
     const int zs = (a.N * 8 + ZT - 1) / ZT;  // Z-update CTAs per (interval, direction)
-    for (int i = threadIdx.x; i < a.I * a.K; i += blockDim.x) {
+    for (int i = threadIdx.x; i < a.I * a.G * a.K; i += blockDim.x) {
         double d2 = 0.0;
         for (int y = 0; y < zs; ++y) d2 += a.dual2[(size_t)i * ZSLOTS + y];
         dual += sqrt(d2);
@@ -236,7 +240,7 @@ __global__ void __launch_bounds__(CT) k_stats(const ConsArgs a) {
         if (it < a.max_iters) {
             double* o = a.stats + (size_t)it * 4;
             o[0] = prim / sqrt(4.0 * a.N) / ((double)a.A * a.K);
-            o[1] = dual / sqrt(4.0 * a.M * a.N) / ((double)a.I * a.K);
+            o[1] = dual / sqrt(4.0 * a.M * a.N) / ((double)a.I * a.G * a.K);
             o[2] = obj;
             o[3] = sqrt(g);
         }
@@ -261,7 +265,7 @@ cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s) {
 cudaError_t launch_zupdate(const ConsArgs& a, cudaStream_t s) {
     const int zs = (a.N * 8 + ZT - 1) / ZT;
     if (zs > ZSLOTS || a.M > MAX_M) return cudaErrorInvalidConfiguration;
-    k_zupdate<<<dim3(a.I * a.K, zs), ZT, 0, s>>>(a);
+    k_zupdate<<<dim3(a.I * a.G * a.K, zs), ZT, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_yupdate(const ConsArgs& a, cudaStream_t s) {

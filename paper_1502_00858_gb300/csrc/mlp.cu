@@ -6,7 +6,8 @@
 // normalised frequency]; the network outputs a correction y and J_init = J_prev + y.
 // Dense layers with ReLU between them; bfloat16 weights and biases (copies of float32 master
 // weights), float32 activations and accumulation; mean squared error; AdamW. Every reduction has
-// a fixed order. The GEMMs are tiled 64x64x16 shared-memory kernels on the FP32 pipe.
+// a fixed order. The GEMMs run on the tensor cores (mma.sync TF32 with a hi/lo split of the float32
+// operands, float32 accumulation), tiled 64x64x16.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -28,65 +29,134 @@ __device__ __forceinline__ float ldf(const __nv_bfloat16* p) { return __bfloat16
 
 // C[M][N] = op(A)[M][K] op(B)[K][N] with an epilogue; A(m,k) = TA ? A[k*lda+m] : A[m*lda+k],
 // B(k,n) = TB ? B[n*ldb+k] : B[k*ldb+n].
+//
+// Tensor cores: warp-level mma.sync m16n8k8 with TF32 operands and float32 accumulation. A TF32
+// value keeps 10 mantissa bits, so a float32 operand x is split into hi = tf32(x) and
+// lo = tf32(x - hi) (x - hi is exact in float32 and lo carries its next 11 bits), and a product is
+// the sum of the partial products hi*hi + hi*lo + lo*hi (the lo*lo term is below float32 round-off;
+// Henry, Tang and Heinecke 2019 use the same three-product split for bfloat16). bfloat16 values
+// (the weights) are exact in TF32 and need no lo part, so a bfloat16 operand costs two products.
+// CTA tile 64 x 64, k-step 16, 4 warps in a 2 x 2 grid of 32 x 32 warp tiles (2 x 4 mma tiles).
+// Operands are staged in shared memory as float32, rows padded to 20 floats: the fragment reads
+// (8 rows x 4 columns a warp) then fall on 32 distinct banks.
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    hi = to_tf32(x);
+    lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+template <typename T> struct IsBf16 { static constexpr bool value = false; };
+template <> struct IsBf16<__nv_bfloat16> { static constexpr bool value = true; };
+
+constexpr int GT_M = 64, GT_N = 64, GT_K = 16, GT_LD = GT_K + 4;
+
 template <typename TAE, typename TBE, bool TA, bool TB, int EPI>
-__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, const TAE* __restrict__ A, int lda,
+__global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const TAE* __restrict__ A, int lda,
                                               const TBE* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
                                               const __nv_bfloat16* __restrict__ bias, const float* __restrict__ mask,
                                               int ldm) {
-    __shared__ float As[16][64 + 4];
-    __shared__ float Bs[16][64 + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
-    float acc[4][4];
+    constexpr bool A_EXACT = IsBf16<TAE>::value, B_EXACT = IsBf16<TBE>::value;
+    __shared__ float As[GT_M][GT_LD];  // As[m][k]
+    __shared__ float Bs[GT_N][GT_LD];  // Bs[n][k]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gid = lane >> 2, tig = lane & 3;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int m0 = blockIdx.y * GT_M, n0 = blockIdx.x * GT_N;
+    float acc[2][4][4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += 16) {
-        for (int e = threadIdx.x; e < 16 * 64; e += 256) {
-            const int kk = e / 64, mm = e % 64;
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+    for (int k0 = 0; k0 < K; k0 += GT_K) {
+        for (int e = threadIdx.x; e < GT_M * GT_K; e += blockDim.x) {
+            // consecutive threads take consecutive elements of whichever index is contiguous in memory
+            const int kk = TA ? e / GT_M : e % GT_K, mm = TA ? e % GT_M : e / GT_K;
             const int m = m0 + mm, k = k0 + kk;
-            As[kk][mm] = (m < M && k < K) ? ldf(TA ? A + (size_t)k * lda + m : A + (size_t)m * lda + k) : 0.f;
-            const int n = n0 + mm;
-            Bs[kk][mm] = (n < N && k < K) ? ldf(TB ? B + (size_t)n * ldb + k : B + (size_t)k * ldb + n) : 0.f;
+            As[mm][kk] = (m < M && k < K) ? ldf(TA ? A + (size_t)k * lda + m : A + (size_t)m * lda + k) : 0.f;
+            const int kb = TB ? e % GT_K : e / GT_N, nn = TB ? e / GT_K : e % GT_N;
+            const int n = n0 + nn, kq = k0 + kb;
+            Bs[nn][kb] = (n < N && kq < K) ? ldf(TB ? B + (size_t)n * ldb + kq : B + (size_t)kq * ldb + n) : 0.f;
         }
         __syncthreads();
 #pragma unroll
-        for (int kk = 0; kk < 16; ++kk) {
-            float a[4], b[4];
+        for (int ks = 0; ks < GT_K; ks += 8) {
+            uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16 + gid;
+                const float v[4] = {As[r][ks + tig], As[r + 8][ks + tig], As[r][ks + tig + 4], As[r + 8][ks + tig + 4]};
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+                for (int q = 0; q < 4; ++q) {
+                    if (A_EXACT) {
+                        ah[i][q] = __float_as_uint(v[q]);
+                        al[i][q] = 0u;
+                    } else {
+                        split_tf32(v[q], ah[i][q], al[i][q]);
+                    }
+                }
+            }
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + j * 8 + gid;
+                const float v[2] = {Bs[c][ks + tig], Bs[c][ks + tig + 4]};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int q = 0; q < 2; ++q) {
+                    if (B_EXACT) {
+                        bh[j][q] = __float_as_uint(v[q]);
+                        bl[j][q] = 0u;
+                    } else {
+                        split_tf32(v[q], bh[j][q], bl[j][q]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    // small terms first, then the leading product
+                    if (!A_EXACT) mma_tf32(acc[i][j], al[i], bh[j]);
+                    if (!B_EXACT) mma_tf32(acc[i][j], ah[i], bl[j]);
+                    mma_tf32(acc[i][j], ah[i], bh[j]);
+                }
         }
         __syncthreads();
     }
+    // accumulator fragment: e = 0, 1 at row gid, columns 2 tig, 2 tig + 1; e = 2, 3 at row gid + 8
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int m = m0 + ty * 4 + i;
-        if (m >= M) continue;
+    for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int n = n0 + tx * 4 + j;
-            if (n >= N) continue;
-            float v = acc[i][j];
-            if (EPI == EPI_BIAS || EPI == EPI_BIAS_RELU) v += __bfloat162float(bias[n]);
-            if (EPI == EPI_BIAS_RELU) v = fmaxf(v, 0.f);
-            if (EPI == EPI_MASK) v = mask[(size_t)m * ldm + n] > 0.f ? v : 0.f;
-            C[(size_t)m * ldc + n] = v;
-        }
-    }
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int m = m0 + wm + i * 16 + gid + (e >> 1) * 8;
+                const int n = n0 + wn + j * 8 + tig * 2 + (e & 1);
+                if (m >= M || n >= N) continue;
+                float v = acc[i][j][e];
+                if (EPI == EPI_BIAS || EPI == EPI_BIAS_RELU) v += __bfloat162float(bias[n]);
+                if (EPI == EPI_BIAS_RELU) v = fmaxf(v, 0.f);
+                if (EPI == EPI_MASK) v = mask[(size_t)m * ldm + n] > 0.f ? v : 0.f;
+                C[(size_t)m * ldc + n] = v;
+            }
 }
 
 template <typename TAE, typename TBE, bool TA, bool TB, int EPI>
 cudaError_t gemm(int M, int N, int K, const TAE* A, int lda, const TBE* B, int ldb, float* C, int ldc,
                  const __nv_bfloat16* bias, const float* mask, int ldm, cudaStream_t s) {
-    dim3 grid((N + 63) / 64, (M + 63) / 64);
-    k_gemm<TAE, TBE, TA, TB, EPI><<<grid, 256, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ldm);
+    dim3 grid((N + GT_N - 1) / GT_N, (M + GT_M - 1) / GT_M);
+    k_gemm<TAE, TBE, TA, TB, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ldm);
     return cudaGetLastError();
 }
 

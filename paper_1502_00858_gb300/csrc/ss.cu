@@ -26,70 +26,12 @@
 // diagonal every station is the second element of at most one slot, so the shared-memory updates
 // of a diagonal are conflict-free (no atomics). The trial pass reads J' and forms the step as
 // x = J' - J (dP_l = x_pl J'_ql^H + J_pl x_ql^H, the same model change).
-#include "calib_internal.cuh"
-#include "tma.cuh"
+#include "ss_common.cuh"
 
 namespace calib {
 namespace {
 
-// One stage = one whole diagonal; one stage in flight while the other is computed (3 and 4 stages
-// measured no faster for the Hessian pass).
-template <bool HV> __host__ __device__ constexpr int nst() { return 2; }
-constexpr int BAR_BYTES = 64;  // barrier area, keeps what follows 16-byte aligned
-constexpr int HV1_KMAX = 5;    // largest K of the one-thread-per-slot Hessian kernel (register budget)
-
-
-__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// acc += s * q
-__device__ __forceinline__ void cmac(float2& acc, float2 s, float2 q) {
-    acc.x = fmaf(s.x, q.x, fmaf(-s.y, q.y, acc.x));
-    acc.y = fmaf(s.x, q.y, fmaf(s.y, q.x, acc.y));
-}
-// acc + a[0] conj(b[0]) + a[1] conj(b[1]) for complex pairs packed as (re, im, re, im), one FMA chain
-// per component (a conj(b) = (a.x b.x + a.y b.y, a.y b.x - a.x b.y)).
-__device__ __forceinline__ float2 cdot2_acc(float2 acc, float4 a, float4 b) {
-    float re = fmaf(a.x, b.x, acc.x);
-    re = fmaf(a.y, b.y, re);
-    re = fmaf(a.z, b.z, re);
-    re = fmaf(a.w, b.w, re);
-    float im = fmaf(a.y, b.x, acc.y);
-    im = fmaf(-a.x, b.y, im);
-    im = fmaf(a.w, b.z, im);
-    im = fmaf(-a.z, b.w, im);
-    return make_float2(re, im);
-}
-// acc + sg (x0 b0 + x1 b1) (complex products; sg = +1 or -1 folded into the FMAs).
-__device__ __forceinline__ float2 cmul2_acc(float2 acc, float sg, float2 x0, float2 b0, float2 x1, float2 b1) {
-    float re = fmaf(sg * x0.x, b0.x, acc.x);
-    re = fmaf(-sg * x0.y, b0.y, re);
-    re = fmaf(sg * x1.x, b1.x, re);
-    re = fmaf(-sg * x1.y, b1.y, re);
-    float im = fmaf(sg * x0.x, b0.y, acc.y);
-    im = fmaf(sg * x0.y, b0.x, im);
-    im = fmaf(sg * x1.x, b1.y, im);
-    im = fmaf(sg * x1.y, b1.x, im);
-    return make_float2(re, im);
-}
-// acc + sg (conj(x0) b0 + conj(x1) b1); conj(x) b = (x.x b.x + x.y b.y, x.x b.y - x.y b.x).
-__device__ __forceinline__ float2 cmul2c_acc(float2 acc, float sg, float2 x0, float2 b0, float2 x1, float2 b1) {
-    float re = fmaf(sg * x0.x, b0.x, acc.x);
-    re = fmaf(sg * x0.y, b0.y, re);
-    re = fmaf(sg * x1.x, b1.x, re);
-    re = fmaf(sg * x1.y, b1.y, re);
-    float im = fmaf(sg * x0.x, b0.y, acc.y);
-    im = fmaf(-sg * x0.y, b0.x, im);
-    im = fmaf(sg * x1.x, b1.y, im);
-    im = fmaf(-sg * x1.y, b1.x, im);
-    return make_float2(re, im);
-}
-__device__ __forceinline__ float4 f4sub(float4 a, float4 b) { return make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w); }
-// value of the partner lane (lane ^ 1: the other row of the same slot)
-__device__ __forceinline__ float2 shfl2x(float2 v) {
-    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1));
-}
-
-// CTA holding item i of W items split into G equal contiguous ranges (start(c) = floor(c W / G)).
-__device__ __forceinline__ long long cta_of_item(long long i, long long W, long long G) { return ((i + 1) * G - 1) / W; }
+using namespace ss;
 
 // KB: register bucket; EXACT: K == KB, so every loop bound and packed-S index is a constant.
 // SMALL: at most 128 threads (N <= 64): 168 registers with 3 CTAs of 128 threads per SM (the trial
@@ -359,206 +301,6 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB
     }
 }
 
-// Hessian pass with one thread per slot (both rows of the 2x2 blocks), for K <= HV1_KMAX: the second
-// station's rows of J and eta are read from shared memory once per slot instead of once per row
-// thread, the first station's other row is in registers, and no partner exchange is needed; the
-// price is twice the registers per thread (both rows of J, eta and the first-station sums).
-// Same partition, copy ring, statistics layout and partial layout as k_ss_sweep.
-// Stage layout: [S: n2][KK] float2.
-// 64 threads (N <= 64) at up to 255 registers: 4 CTAs, 8 warps per SM.
-template <int KB>
-__global__ void __launch_bounds__(128, 2) k_ss_hessvec(const SSArgs a, const int stage_bytes) {
-    constexpr int NST = nst<true>();
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int N = a.N, D = a.D, NP = a.NP;
-    constexpr int K = KB;
-    const int KK = K * (K + 1) / 2;
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    const int g = tid;
-    const int KN2 = K * N * 2;
-    const bool own = g < N;
-
-    unsigned char* stage = smem;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + NST * stage_bytes);
-    // [K][2 rows][N]: consecutive threads read consecutive 16-byte entries (no bank conflicts)
-    float4* Js = reinterpret_cast<float4*>(smem + NST * stage_bytes + BAR_BYTES);
-    float4* Es = Js + KN2;
-    float4* accs = Es + KN2;
-
-    const long long W = (long long)a.A * D, G = gridDim.x;
-    const long long i0 = (long long)blockIdx.x * W / G;
-    const int S = (int)((long long)(blockIdx.x + 1) * W / G - i0);
-    const int ag0 = (int)(i0 / D), d0 = (int)(i0 - (long long)ag0 * D);
-
-    if (tid == 0) {
-        for (int i = 0; i < NST; ++i) mbar_init(&bar[i], 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-
-    int iss_ag = ag0, iss_d = d0;
-    const uint64_t pol = tid == 0 ? l2_evict_first() : 0ull;
-    auto issue = [&](int s2) {
-        const size_t blk = ((size_t)iss_ag * D + iss_d) * NP;
-        const int n = (2 * (iss_d + 1) == N) ? N / 2 : N;
-        const int n2 = (n + 1) & ~1;
-        if (++iss_d == D) { iss_d = 0; ++iss_ag; }
-        const uint32_t sb = (uint32_t)(n2 * KK * 8);
-        uint64_t* b = &bar[s2 % NST];
-        mbar_expect_tx(b, sb);
-        bulk_g2s_stream(stage + (s2 % NST) * stage_bytes, a.S + blk * KK, sb, b, pol);
-    };
-    if (tid == 0)
-        for (int s2 = 0; s2 < min(NST - 1, S); ++s2) issue(s2);
-
-    float4 Jf[KB][2], Ef[KB][2], A1[KB][2];  // station g's rows of J and eta; its first-station sums
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-    for (int k = 0; k < KB; ++k)
-#pragma unroll
-        for (int r = 0; r < 2; ++r) Jf[k][r] = Ef[k][r] = A1[k][r] = z4;
-
-    auto flush = [&](int ag) {
-        const long long piece = blockIdx.x - cta_of_item((long long)ag * D, W, G);
-        const size_t slot_p = (size_t)ag * a.part_stride + (size_t)piece;
-        float4* out = reinterpret_cast<float4*>(a.part) + slot_p * KN2;
-        if (own) {
-#pragma unroll
-            for (int k = 0; k < KB; ++k) {
-                if (k >= K) continue;
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const float4 w = accs[(k * 2 + r) * N + g];
-                    out[(k * N + g) * 2 + r] = make_float4(A1[k][r].x + w.x, A1[k][r].y + w.y, A1[k][r].z + w.z, A1[k][r].w + w.w);
-                }
-            }
-        }
-    };
-
-    int agent = -1, ag = ag0, dg = d0;
-    bool fresh = false;
-    for (int s = 0; s < S; ++s) {
-        if (ag != agent) {
-            if (agent >= 0) {
-                __syncthreads();
-                flush(agent);
-                __syncthreads();
-            }
-            agent = ag;
-            fresh = true;
-            const float4* Jg = reinterpret_cast<const float4*>(a.J) + (size_t)ag * KN2;
-            const float4* Eg = reinterpret_cast<const float4*>(a.eta) + (size_t)ag * KN2;
-            for (int i = tid; i < KN2; i += nthr) {  // global [K][N][2] -> shared [K][2][N]
-                const int r = i & 1, kn = i >> 1, kk = kn / N, st = kn - kk * N;
-                const int o = (kk * 2 + r) * N + st;
-                Js[o] = __ldg(Jg + i);
-                Es[o] = __ldg(Eg + i);
-                accs[i] = z4;
-            }
-        }
-        const int d = dg + 1;
-        if (++dg == D) { dg = 0; ++ag; }
-        const bool ok = mbar_wait_bounded(&bar[s % NST], (uint32_t)((s / NST) & 1));
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicOr(a.status, STATUS_TIMEOUT);
-                const int last = min(S - 1, s + NST - 1);
-                for (int s2 = s; s2 <= last; ++s2) mbar_wait_bounded(&bar[s2 % NST], (uint32_t)((s2 / NST) & 1));
-            }
-            return;
-        }
-        if (tid == 0 && s + NST - 1 < S) {
-            fence_proxy_async_smem();
-            issue(s + NST - 1);
-        }
-        if (fresh) {
-            fresh = false;
-            if (own) {
-#pragma unroll
-                for (int k = 0; k < KB; ++k) {
-                    if (k >= K) continue;
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        Jf[k][r] = Js[(k * 2 + r) * N + g];
-                        Ef[k][r] = Es[(k * 2 + r) * N + g];
-                        A1[k][r] = z4;
-                    }
-                }
-            }
-        }
-        const int n = (2 * d == N) ? N / 2 : N;
-        if (g >= n) continue;
-        const float2* Ss = reinterpret_cast<const float2*>(stage + (s % NST) * stage_bytes) + (size_t)g * KK;
-        const int second = (g + d < N) ? g + d : g + d - N;
-        // X_k = (S Q)_k, entries [row][column] at 2 row + column
-        float2 X[KB][4];
-#pragma unroll
-        for (int k = 0; k < KB; ++k)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) X[k][e] = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int l = 0; l < KB; ++l) {
-            if (l >= K) continue;
-            // Q_l = eta_f J_s^H + J_f eta_s^H; (A B^H)[r][c] = A[r][0] conj(B[c][0]) + A[r][1] conj(B[c][1])
-            const float4 js0 = Js[2 * l * N + second], js1 = Js[(2 * l + 1) * N + second];
-            const float4 es0 = Es[2 * l * N + second], es1 = Es[(2 * l + 1) * N + second];
-            const float2 z2 = make_float2(0.f, 0.f);
-            float2 q[4];
-            q[0] = cdot2_acc(cdot2_acc(z2, Ef[l][0], js0), Jf[l][0], es0);
-            q[1] = cdot2_acc(cdot2_acc(z2, Ef[l][0], js1), Jf[l][0], es1);
-            q[2] = cdot2_acc(cdot2_acc(z2, Ef[l][1], js0), Jf[l][1], es0);
-            q[3] = cdot2_acc(cdot2_acc(z2, Ef[l][1], js1), Jf[l][1], es1);
-#pragma unroll
-            for (int k = 0; k < KB; ++k) {
-                if (k >= K) continue;
-                const int lo = k < l ? k : l, hi = k < l ? l : k;
-                float2 skl = Ss[lo * K - lo * (lo - 1) / 2 + (hi - lo)];
-                if (k > l) skl.y = -skl.y;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) cmac(X[k][e], skl, q[e]);
-            }
-        }
-        // Station terms. First station (registers): (X_k J_s)[r][.] = X[r][0] J_s[0][.] + X[r][1] J_s[1][.].
-#pragma unroll
-        for (int k = 0; k < KB; ++k) {
-            if (k >= K) continue;
-            const float4 s0 = Js[2 * k * N + second], s1 = Js[(2 * k + 1) * N + second];
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const float2 a0 = cmul2_acc(make_float2(A1[k][r].x, A1[k][r].y), 1.f, X[k][2 * r], make_float2(s0.x, s0.y),
-                                            X[k][2 * r + 1], make_float2(s1.x, s1.y));
-                const float2 a1 = cmul2_acc(make_float2(A1[k][r].z, A1[k][r].w), 1.f, X[k][2 * r], make_float2(s0.z, s0.w),
-                                            X[k][2 * r + 1], make_float2(s1.z, s1.w));
-                A1[k][r] = make_float4(a0.x, a0.y, a1.x, a1.y);
-            }
-        }
-        // Second station (shared): (X_k^H J_f)[r][.] = conj(X[0][r]) J_f[0][.] + conj(X[1][r]) J_f[1][.].
-        // Every sum is read before any is written: the compiler cannot tell the directions'
-        // addresses apart and would otherwise wait for each store before the next load.
-        float4 t2[KB][2];
-#pragma unroll
-        for (int k = 0; k < KB; ++k)
-#pragma unroll
-            for (int r = 0; r < 2; ++r) t2[k][r] = k < K ? accs[(k * 2 + r) * N + second] : z4;
-#pragma unroll
-        for (int k = 0; k < KB; ++k) {
-            if (k >= K) continue;
-#pragma unroll
-            for (int r = 0; r < 2; ++r) {
-                const float2 b0 = cmul2c_acc(make_float2(t2[k][r].x, t2[k][r].y), 1.f, X[k][r], make_float2(Jf[k][0].x, Jf[k][0].y),
-                                             X[k][2 + r], make_float2(Jf[k][1].x, Jf[k][1].y));
-                const float2 b1 = cmul2c_acc(make_float2(t2[k][r].z, t2[k][r].w), 1.f, X[k][r], make_float2(Jf[k][0].z, Jf[k][0].w),
-                                             X[k][2 + r], make_float2(Jf[k][1].z, Jf[k][1].w));
-                accs[(k * 2 + r) * N + second] = make_float4(b0.x, b0.y, b1.x, b1.y);
-            }
-        }
-    }
-    if (agent >= 0) {
-        __syncthreads();
-        flush(agent);
-    }
-}
-
 template <int KB, bool HV>
 cudaError_t prep_kb() {
     const auto attr = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -568,12 +310,6 @@ cudaError_t prep_kb() {
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ss_sweep<KB, HV, false, true>, attr, 200 * 1024);
     return e;
 }
-
-template <int KB>
-cudaError_t prep_hv1() {
-    return cudaFuncSetAttribute(k_ss_hessvec<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-}
-
 template <bool HV>
 cudaError_t prep_all() {
     cudaError_t e;
@@ -604,24 +340,6 @@ cudaError_t go(const SSArgs& a, int grid, int threads, size_t smem, int sb, cuda
         k_ss_sweep<KB, HV, false, false><<<grid, threads, smem, s>>>(a, sb);
     return cudaGetLastError();
 }
-
-template <int KB>
-cudaError_t go_hv1(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
-    k_ss_hessvec<KB><<<grid, threads, smem, s>>>(a, sb);
-    return cudaGetLastError();
-}
-
-cudaError_t dispatch_hv1(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
-    static_assert(HV1_KMAX == 5, "dispatch_hv1 covers K = 1 .. 5");
-    switch (a.K) {
-        case 1: return go_hv1<1>(a, grid, threads, smem, sb, s);
-        case 2: return go_hv1<2>(a, grid, threads, smem, sb, s);
-        case 3: return go_hv1<3>(a, grid, threads, smem, sb, s);
-        case 4: return go_hv1<4>(a, grid, threads, smem, sb, s);
-        default: return go_hv1<5>(a, grid, threads, smem, sb, s);
-    }
-}
-
 template <bool HV>
 cudaError_t dispatch(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
     const int K = a.K;
@@ -644,11 +362,7 @@ cudaError_t dispatch(const SSArgs& a, int grid, int threads, size_t smem, int sb
 cudaError_t prepare_ss_kernels() {
     cudaError_t e = prep_all<false>();
     if (e == cudaSuccess) e = prep_all<true>();
-    if (e == cudaSuccess) e = prep_hv1<1>();
-    if (e == cudaSuccess) e = prep_hv1<2>();
-    if (e == cudaSuccess) e = prep_hv1<3>();
-    if (e == cudaSuccess) e = prep_hv1<4>();
-    if (e == cudaSuccess) e = prep_hv1<5>();
+    if (e == cudaSuccess) e = prepare_ss_hessvec_kernels();
     return e;
 }
 
@@ -669,7 +383,7 @@ cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, int grid, cudaStream_
     int sb = 0;
     const size_t smem = ss_sweep_smem_bytes(a.N, a.K, hessvec, &sb);
     if (smem > 200 * 1024 || grid < 1 || (long long)grid > (long long)a.A * a.D) return cudaErrorInvalidConfiguration;
-    if (hessvec && a.K <= HV1_KMAX) return dispatch_hv1(a, grid, (a.N + 31) / 32 * 32, smem, sb, s);
+    if (hessvec && a.K <= HV1_KMAX) return launch_ss_hessvec1(a, grid, (a.N + 31) / 32 * 32, smem, sb, s);
     const int threads = ss_sweep_threads(a.N);
     return hessvec ? dispatch<true>(a, grid, threads, smem, sb, s) : dispatch<false>(a, grid, threads, smem, sb, s);
 }
