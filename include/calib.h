@@ -222,7 +222,8 @@ int calib_sync(calib_ctx* ctx);
  * Kinds: sweep_residual (direct residual/trial), sweep_hessvec (direct Hessian), stats_hessvec and
  * stats_trial (sufficient-statistics passes), pcg_step and lm_eval (per-agent LM kernels, no
  * algorithmic byte or flop count: 0), stats_pass (forming the statistics from V and C, timed
- * outside the graph when calib_admm_iter runs it); bytes_per_launch and flops_per_launch are the
+ * outside the graph when calib_admm_iter runs it), consensus (the gauge projection, Z-update,
+ * Y-update and records of one iteration, timed as one); bytes_per_launch and flops_per_launch are the
  * algorithmic bytes and real flops (complex multiply 6, complex multiply-add 8) of one launch.
  * Every output array may be NULL and receives up to cap entries; returns the number of kinds. */
 int calib_profile_enable(calib_ctx* ctx, int on);
@@ -231,7 +232,7 @@ int calib_profile_read(calib_ctx* ctx, int cap, const char** names, double* tota
 
 /* Autotuner: time the two halves of one LM step on the loaded data - n_cg Hessian passes with
  * their PCG steps, and the trial pass with its reduction - for each candidate work split. The
- * split is CTAs per SM (1, 2, 3, 4, 6, 8, 12, 16, 24) for CALIB_FORM_STATISTICS, chosen per pass,
+ * split is CTAs per SM (1, 2, 3, 4, 5, 6, 8, 12, 16, 24) for CALIB_FORM_STATISTICS, chosen per pass,
  * and diagonals per CTA (1, 2, 4, ..., N/2) for CALIB_FORM_DIRECT, one value for both passes (the
  * fastest whole step). calib_admm_iter runs it by itself before its first iteration when the
  * option that fixes the split (ctas_per_sm or chunk_diagonals) is 0; the choice is cached per

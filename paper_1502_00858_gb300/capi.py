@@ -273,7 +273,7 @@ def calib_profile_enable(ctx, on: bool):
 
 
 def calib_profile_read(ctx):
-    cap = 8
+    cap = 16
     names = (C.c_char_p * cap)()
     ms = np.zeros(cap)
     n = np.zeros(cap, dtype=np.int64)

@@ -108,8 +108,8 @@ struct calib_ctx {
     std::vector<int> slot_h, slot_b_h;
     long long int_v = 0, int_c = 0;             // internal totals (float2)
     long long int_u = 0, int_s = 0;             // sufficient-statistics totals (float2)
-    double alg_bytes[7] = {0, 0, 0, 0, 0, 0, 0};  // algorithmic bytes per launch of each profiled kind
-    double alg_flops[7] = {0, 0, 0, 0, 0, 0, 0};  // algorithmic real flops per launch of each profiled kind
+    double alg_bytes[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // algorithmic bytes per launch of each profiled kind
+    double alg_flops[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // algorithmic real flops per launch of each profiled kind
     std::vector<uint8_t> flags_h;
 
     // device
@@ -156,9 +156,11 @@ struct calib_ctx {
     std::map<std::tuple<int, int, int, int>, GraphEntry> graphs;
     long long launches = 0;
     bool profiling = false;
-    static constexpr int PROF_KINDS = 7;  // 4 sweep kinds, the PCG step, the LM evaluation, the statistics pass
-    double prof_ms[PROF_KINDS] = {0, 0, 0, 0, 0, 0, 0};
-    long long prof_n[PROF_KINDS] = {0, 0, 0, 0, 0, 0, 0};
+    // 4 sweep kinds, the PCG step, the LM evaluation, the statistics pass, the fusion-centre step
+    // (gauge, Z-update, Y-update and records of one iteration, timed together)
+    static constexpr int PROF_KINDS = 8;
+    double prof_ms[PROF_KINDS] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long prof_n[PROF_KINDS] = {0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
@@ -650,10 +652,12 @@ void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
         q.sweep(SWEEP_TRIAL, c->J, c->x);
         q.lm_eval(la, LM_ACCEPT);
     }
+    ProfPair pp = q.begin(7);
     if (gauge) q.ok(launch_gauge(ca, c->stream));
     q.ok(launch_zupdate(ca, c->stream));
     q.ok(launch_yupdate(ca, c->stream));
     q.ok(launch_stats(ca, c->stream));
+    q.end(pp);
 }
 
 int ensure_stats(calib_ctx* c, int n) {
@@ -717,7 +721,7 @@ int autotune(calib_ctx* c) {
     if (c->formulation == 0) {
         const long long W = (long long)c->A * c->D;
         long long last_grid = -1;
-        for (int m : {1, 2, 3, 4, 6, 8, 12, 16, 24}) {
+        for (int m : {1, 2, 3, 4, 5, 6, 8, 12, 16, 24}) {
             const long long grid = std::min(W, (long long)c->sms * m);
             if (grid == last_grid) break;  // capped at one item per CTA
             cands.push_back(m);
@@ -1494,7 +1498,8 @@ int calib_profile_read(calib_ctx* c, int cap, const char** names, double* total_
                        double* bytes_per_launch, double* flops_per_launch) {
     if (!c) return fail(CALIB_EINVAL, "ctx is NULL");
     static const char* kNames[calib_ctx::PROF_KINDS] = {"sweep_residual", "sweep_hessvec", "stats_hessvec",
-                                                          "stats_trial", "pcg_step", "lm_eval", "stats_pass"};
+                                                          "stats_trial", "pcg_step", "lm_eval", "stats_pass",
+                                                          "consensus"};
     for (int i = 0; i < calib_ctx::PROF_KINDS && i < cap; ++i) {
         if (names) names[i] = kNames[i];
         if (total_ms) total_ms[i] = c->prof_ms[i];

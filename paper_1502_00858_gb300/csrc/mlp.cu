@@ -60,19 +60,24 @@ template <typename T> struct IsBf16 { static constexpr bool value = false; };
 template <> struct IsBf16<__nv_bfloat16> { static constexpr bool value = true; };
 
 constexpr int GT_M = 64, GT_N = 64, GT_K = 16, GT_LD = GT_K + 4;
+constexpr int SPLITK_MAX = 16;  // K-splits of a weight-gradient product
 
 template <typename TAE, typename TBE, bool TA, bool TB, int EPI>
 __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const TAE* __restrict__ A, int lda,
                                               const TBE* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
                                               const __nv_bfloat16* __restrict__ bias, const float* __restrict__ mask,
-                                              int ldm) {
+                                              int ldm, int k_chunk) {
     constexpr bool A_EXACT = IsBf16<TAE>::value, B_EXACT = IsBf16<TBE>::value;
+    constexpr int PER = GT_M * GT_K / 128;  // tile elements a thread stages per operand
     __shared__ float As[GT_M][GT_LD];  // As[m][k]
     __shared__ float Bs[GT_N][GT_LD];  // Bs[n][k]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gid = lane >> 2, tig = lane & 3;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int m0 = blockIdx.y * GT_M, n0 = blockIdx.x * GT_N;
+    // split-K: this CTA sums k in [kb, ke) and writes its partial to C + blockIdx.z * M * ldc
+    const int kb = blockIdx.z * k_chunk, ke = min(K, kb + k_chunk);
+    float* Cz = C + (size_t)blockIdx.z * M * ldc;
     float acc[2][4][4];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -80,17 +85,45 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const TAE* __
         for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-    for (int k0 = 0; k0 < K; k0 += GT_K) {
-        for (int e = threadIdx.x; e < GT_M * GT_K; e += blockDim.x) {
-            // consecutive threads take consecutive elements of whichever index is contiguous in memory
-            const int kk = TA ? e / GT_M : e % GT_K, mm = TA ? e % GT_M : e / GT_K;
+    // staging map: consecutive threads take consecutive elements of the index contiguous in memory
+    auto a_at = [](int e, int& mm, int& kk) {
+        kk = TA ? e / GT_M : e % GT_K;
+        mm = TA ? e % GT_M : e / GT_K;
+    };
+    auto b_at = [](int e, int& nn, int& kk) {
+        kk = TB ? e % GT_K : e / GT_N;
+        nn = TB ? e / GT_K : e % GT_N;
+    };
+    float ra[PER], rb[PER];  // the next k-tile, fetched while the current one is multiplied
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = threadIdx.x + q * 128;
+            int mm, kk, nn, kq;
+            a_at(e, mm, kk);
             const int m = m0 + mm, k = k0 + kk;
-            As[mm][kk] = (m < M && k < K) ? ldf(TA ? A + (size_t)k * lda + m : A + (size_t)m * lda + k) : 0.f;
-            const int kb = TB ? e % GT_K : e / GT_N, nn = TB ? e / GT_K : e % GT_N;
-            const int n = n0 + nn, kq = k0 + kb;
-            Bs[nn][kb] = (n < N && kq < K) ? ldf(TB ? B + (size_t)n * ldb + kq : B + (size_t)kq * ldb + n) : 0.f;
+            ra[q] = (m < M && k < ke) ? ldf(TA ? A + (size_t)k * lda + m : A + (size_t)m * lda + k) : 0.f;
+            b_at(e, nn, kq);
+            const int n = n0 + nn, k2 = k0 + kq;
+            rb[q] = (n < N && k2 < ke) ? ldf(TB ? B + (size_t)n * ldb + k2 : B + (size_t)k2 * ldb + n) : 0.f;
         }
+    };
+    auto stage = [&]() {
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int e = threadIdx.x + q * 128;
+            int mm, kk, nn, kq;
+            a_at(e, mm, kk);
+            As[mm][kk] = ra[q];
+            b_at(e, nn, kq);
+            Bs[nn][kq] = rb[q];
+        }
+    };
+    if (kb < ke) fetch(kb);
+    for (int k0 = kb; k0 < ke; k0 += GT_K) {
+        stage();
         __syncthreads();
+        if (k0 + GT_K < ke) fetch(k0 + GT_K);
 #pragma unroll
         for (int ks = 0; ks < GT_K; ks += 8) {
             uint32_t ah[2][4], al[2][4], bh[4][2], bl[4][2];
@@ -148,15 +181,44 @@ __global__ void __launch_bounds__(128) k_gemm(int M, int N, int K, const TAE* __
                 if (EPI == EPI_BIAS || EPI == EPI_BIAS_RELU) v += __bfloat162float(bias[n]);
                 if (EPI == EPI_BIAS_RELU) v = fmaxf(v, 0.f);
                 if (EPI == EPI_MASK) v = mask[(size_t)m * ldm + n] > 0.f ? v : 0.f;
-                C[(size_t)m * ldc + n] = v;
+                Cz[(size_t)m * ldc + n] = v;
             }
 }
 
+// C = sum of the split-K partials in split order (a fixed order: results do not depend on timing).
+__global__ void k_sum_splits(const float* part, int splits, long long n, float* C) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = part[i];
+        for (int z = 1; z < splits; ++z) s += part[(size_t)z * n + i];
+        C[i] = s;
+    }
+}
+
+// One CTA per 64 x 64 output tile over all of K.
 template <typename TAE, typename TBE, bool TA, bool TB, int EPI>
 cudaError_t gemm(int M, int N, int K, const TAE* A, int lda, const TBE* B, int ldb, float* C, int ldc,
                  const __nv_bfloat16* bias, const float* mask, int ldm, cudaStream_t s) {
-    dim3 grid((N + GT_N - 1) / GT_N, (M + GT_M - 1) / GT_M);
-    k_gemm<TAE, TBE, TA, TB, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ldm);
+    dim3 grid((N + GT_N - 1) / GT_N, (M + GT_M - 1) / GT_M, 1);
+    k_gemm<TAE, TBE, TA, TB, EPI><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, C, ldc, bias, mask, ldm,
+                                                        (K + GT_K - 1) / GT_K * GT_K);
+    return cudaGetLastError();
+}
+
+// Split-K for a product with few output tiles and a long K (the weight gradients, K = rows): up to
+// `splits` CTAs per tile, each over a 16-aligned share of K, their partials summed by k_sum_splits.
+// work: splits * M * N floats; C is a dense M x N array.
+template <typename TAE, typename TBE, bool TA, bool TB>
+cudaError_t gemm_splitk(int M, int N, int K, const TAE* A, int lda, const TBE* B, int ldb, float* C, float* work,
+                        int splits, cudaStream_t s) {
+    const int chunk = ((K + splits - 1) / splits + GT_K - 1) / GT_K * GT_K;
+    splits = chunk > 0 ? (K + chunk - 1) / chunk : 1;
+    if (splits <= 1) return gemm<TAE, TBE, TA, TB, EPI_STORE>(M, N, K, A, lda, B, ldb, C, N, nullptr, nullptr, 0, s);
+    dim3 grid((N + GT_N - 1) / GT_N, (M + GT_M - 1) / GT_M, splits);
+    k_gemm<TAE, TBE, TA, TB, EPI_STORE><<<grid, 128, 0, s>>>(M, N, K, A, lda, B, ldb, work, N, nullptr, nullptr, 0, chunk);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)M * N;
+    k_sum_splits<<<(unsigned)std::min<long long>((n + 255) / 256, 1024), 256, 0, s>>>(work, splits, n, C);
     return cudaGetLastError();
 }
 
@@ -276,6 +338,8 @@ struct MlpNet {
     int cap = 0;
     std::vector<float*> act;
     float *X = nullptr, *T = nullptr, *g1 = nullptr, *g2 = nullptr, *pred = nullptr;
+    float* splitk = nullptr;  // split-K partials of the weight gradients: SPLITK_MAX x the largest layer
+    int sms = 1;              // SM count of the device
     double *part = nullptr, *loss = nullptr;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
@@ -337,9 +401,11 @@ cudaError_t backward(MlpNet* n, const float* X, const float* T, int rows) {
     for (int l = L - 1; l >= 0 && e == cudaSuccess; --l) {
         const float* h_in = l == 0 ? X : n->act[l - 1];
         const int in = n->in_dim[l], out = n->out_dim[l];
-        // dW = g^T h_in  (out x in)
-        e = gemm<float, float, true, false, EPI_STORE>(out, in, rows, g, out, h_in, in, n->grad + n->off_w[l], in,
-                                                       nullptr, nullptr, 0, n->stream);
+        // dW = g^T h_in  (out x in): few output tiles over a long K (the rows), so split K
+        const int tiles = ((out + GT_M - 1) / GT_M) * ((in + GT_N - 1) / GT_N);
+        const int splits = std::max(1, std::min(SPLITK_MAX, 2 * n->sms / tiles));  // about two CTAs per SM
+        e = gemm_splitk<float, float, true, false>(out, in, rows, g, out, h_in, in, n->grad + n->off_w[l], n->splitk,
+                                                   splits, n->stream);
         if (e != cudaSuccess) break;
         k_colsum<<<(out + 31) / 32, 256, 0, n->stream>>>(g, rows, out, n->grad + n->off_b[l]);
         e = cudaGetLastError();
@@ -412,6 +478,12 @@ int calib_mlp_create(calib_mlp** out, int n_in, int width, int depth, int n_out,
     if (e == cudaSuccess) e = cudaMalloc(&n->v, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&n->grad, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&n->part, 4096 * sizeof(double));
+    long long largest = 0;
+    for (size_t l = 0; l < n->in_dim.size(); ++l) largest = std::max(largest, (long long)n->in_dim[l] * n->out_dim[l]);
+    if (e == cudaSuccess) e = cudaMalloc(&n->splitk, (size_t)calib::SPLITK_MAX * largest * sizeof(float));
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n->sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaMalloc(&n->loss, sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(n->master, 0, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(n->wb, 0, off * sizeof(__nv_bfloat16));
@@ -511,7 +583,7 @@ void calib_mlp_destroy(calib_mlp* h) {
     MlpNet* n = &h->net;
     if (n->stream) cudaStreamSynchronize(n->stream);
     for (float* p : n->act) cudaFree(p);
-    for (void* p : {(void*)n->master, (void*)n->wb, (void*)n->m, (void*)n->v, (void*)n->grad, (void*)n->X, (void*)n->T,
+    for (void* p : {(void*)n->master, (void*)n->wb, (void*)n->m, (void*)n->v, (void*)n->grad, (void*)n->splitk, (void*)n->X, (void*)n->T,
                     (void*)n->g1, (void*)n->g2, (void*)n->pred, (void*)n->part, (void*)n->loss})
         if (p) cudaFree(p);
     if (n->own_stream && n->stream) cudaStreamDestroy(n->stream);
