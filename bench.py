@@ -398,6 +398,19 @@ def run_ours(args, world, rank, local):
             "share_of_step": v["total_ms"] / 1e3 / dt if dt else None}
         for k, v in prof.items()}
 
+    # coherency prediction (once per step), after the timed region
+    for _ in range(2):
+        capi.calib_predict(cal.ctx, uvw_d, sky_d, prob["f0"])
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(5):
+        capi.calib_predict(cal.ctx, uvw_d, sky_d, prob["f0"])
+    p1.record(stream)
+    torch.cuda.synchronize()
+    roofline["predict"] = {"avg_launch_us": p0.elapsed_time(p1) * 1e3 / 5,
+                           "note": "coherencies of every (baseline, sample, direction) from the sky model, "
+                                   "with the Jacobi weights they imply; once per step"}
+
     # residual visibilities of every direction at the final solutions (Section 2), after the timed
     # region: one HBM stream reading V and C and writing R once per visibility
     out_d = torch.empty(int(vis_d.numel()), dtype=torch.float32, device=dev)

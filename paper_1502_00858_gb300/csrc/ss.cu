@@ -41,10 +41,12 @@ using namespace ss;
 // Stage layout: [U: n2][K][2 rows] float4 (trial only) | [S: n2][KK] float2, n2 = the diagonal's slot
 // count rounded up to even.
 template <int KB, bool HV, bool EXACT, bool SMALL>
-__global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB >= 8 ? 2 : 3)) : (HV ? 2 : 1))
+__global__ void __launch_bounds__(SMALL ? 128 : 256,
+                                  SMALL ? (KB >= 10 ? (ss_u_global(HV, KB) ? 2 : 1) : (KB >= 8 ? 2 : 3)) : (HV ? 2 : 1))
     k_ss_sweep(const SSArgs a, const int stage_bytes) {
     constexpr int NST = nst<HV>();
     constexpr float sg = HV ? 1.f : -1.f;  // station terms: + in the Hessian pass, - (gradient) in the trial pass
+    constexpr bool UG = ss_u_global(HV, KB);  // the trial pass reads U from global memory (not staged)
     extern __shared__ __align__(128) unsigned char smem[];
     const int N = a.N, D = a.D, NP = a.NP;
     const int K = EXACT ? KB : a.K;
@@ -81,7 +83,7 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB
         const int n = (2 * (iss_d + 1) == N) ? N / 2 : N;
         const int n2 = (n + 1) & ~1;  // an even slot count keeps both copies multiples of 16 bytes
         if (++iss_d == D) { iss_d = 0; ++iss_ag; }
-        const uint32_t ub = HV ? 0u : (uint32_t)(n2 * K * 32);
+        const uint32_t ub = (HV || UG) ? 0u : (uint32_t)(n2 * K * 32);
         const uint32_t sb = (uint32_t)(n2 * KK * 8);
         unsigned char* buf = stage + (s2 % NST) * stage_bytes;
         uint64_t* b = &bar[s2 % NST];
@@ -176,8 +178,9 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB
         const int n = (2 * d == N) ? N / 2 : N;
         const int n2 = (n + 1) & ~1;
         const unsigned char* buf = stage + (s % NST) * stage_bytes;
-        const float2* Us = reinterpret_cast<const float2*>(buf);  // [n2][K][2][2] (trial)
-        const float2* Ss = reinterpret_cast<const float2*>(buf + (HV ? 0 : n2 * K * 32)) + (size_t)g * KK;
+        // U of this diagonal [n2][K][2][2] (trial): staged, or read from global memory (UG)
+        const float2* Us = UG ? a.U + ((size_t)agent * D + (d - 1)) * NP * K * 4 : reinterpret_cast<const float2*>(buf);
+        const float2* Ss = reinterpret_cast<const float2*>(buf + ((HV || UG) ? 0 : n2 * K * 32)) + (size_t)g * KK;
         const bool active = g < n;
         const int second = (g + d < N) ? g + d : g + d - N;
         // Row rr of X_k in column order (rr, 1 - rr): Hessian (S Q)_k; trial W'_k = U_k - (S P)_k - (S dP)_k.
@@ -233,8 +236,9 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256, SMALL ? (KB >= 10 ? 1 : (KB
                 for (int k = 0; k < KB; ++k) {
                     if (k >= K) continue;
                     const float2* u = Us + (((size_t)g * K + k) * 2 + rr) * 2;
-                    const float2 Wd = f2sub(u[rr], Xd[k]);  // W_k at J
-                    const float2 Wo = f2sub(u[ro], Xo[k]);
+                    const float2 ud = UG ? __ldg(u + rr) : u[rr], uo = UG ? __ldg(u + ro) : u[ro];
+                    const float2 Wd = f2sub(ud, Xd[k]);  // W_k at J
+                    const float2 Wo = f2sub(uo, Xo[k]);
                     // decrease: Re[conj(dP_k) (2 W_k - (S dP)_k)], this row
                     dcf = fmaf(dPd[k].x, 2.f * Wd.x - Yd[k].x, fmaf(dPd[k].y, 2.f * Wd.y - Yd[k].y, dcf));
                     dcf = fmaf(dPo[k].x, 2.f * Wo.x - Yo[k].x, fmaf(dPo[k].y, 2.f * Wo.y - Yo[k].y, dcf));
@@ -368,7 +372,7 @@ cudaError_t prepare_ss_kernels() {
 
 size_t ss_sweep_smem_bytes(int N, int K, bool hessvec, int* stage_bytes) {
     const int KK = K * (K + 1) / 2, N2 = (N + 1) / 2 * 2;  // slots copied per stage (even)
-    const int per_slot = (hessvec ? 0 : K * 32) + KK * 8;
+    const int per_slot = ((hessvec || ss_u_global(false, ss_bucket(K))) ? 0 : K * 32) + KK * 8;
     const int sb = ((N2 * per_slot + 127) / 128) * 128;
     if (stage_bytes) *stage_bytes = sb;
     const int nstages = hessvec ? nst<true>() : nst<false>();

@@ -64,6 +64,15 @@ __device__ __forceinline__ float2 shfl2x(float2 v) {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1));
 }
 
+// Register bucket of the statistics sweeps for K directions (the dispatch in ss.cu).
+__host__ __device__ constexpr int ss_bucket(int K) {
+    return K <= 6 ? K : (K <= 8 ? 8 : (K <= 10 ? 10 : (K <= 12 ? 12 : 16)));
+}
+// From bucket 10 on, the trial pass reads U (each entry once) from global memory instead of staging
+// it with the S statistics: a stage of one diagonal's U and S at K = 10 (47 KB) leaves shared memory
+// for one CTA per SM, the S stage alone (27 KB) for two.
+__host__ __device__ constexpr bool ss_u_global(bool hessvec, int kb) { return !hessvec && kb >= 10; }
+
 // CTA holding item i of W items split into G equal contiguous ranges (start(c) = floor(c W / G)).
 __device__ __forceinline__ long long cta_of_item(long long i, long long W, long long G) { return ((i + 1) * G - 1) / W; }
 

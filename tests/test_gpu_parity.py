@@ -79,11 +79,10 @@ CASES = {
     "n10_k16": lambda: make_problem("adjoint_n16_k3", N=10, K=16, P=4, I=1, T=2, seed=26),
     # the largest station count (8128 baselines; 256-thread trial sweep, 128-thread Hessian sweep)
     "n128_k2": lambda: make_problem("adjoint_n16_k3", N=128, K=2, P=4, I=1, T=1, seed=27),
-    # the paper's 47-station array with 16 directions: beyond the statistics sweeps' shared memory,
-    # so only the direct formulation takes it
+    # the paper's 47-station array with 16 directions (the trial pass reads U from global memory)
     "n47_k16": lambda: make_problem("adjoint_n16_k3", N=47, K=16, P=4, I=1, T=2, seed=28),
 }
-DIRECT_ONLY = {"n47_k16"}
+DIRECT_ONLY = set()
 
 
 def form_kw(case):
@@ -234,13 +233,16 @@ def test_predict_full_size_lofar_sample(lib):
 
 
 def test_statistics_form_rejects_shapes_beyond_its_shared_memory(lib):
-    """47 stations x 16 directions need more shared memory than the statistics sweeps have:
-    calib_init refuses that formulation with CALIB_EINVAL and names the direct one."""
-    prob = CASES["n47_k16"]()
+    """64 stations x 16 directions need more shared memory than the statistics sweeps have:
+    calib_init refuses that formulation with CALIB_EINVAL and names the direct one, which takes it."""
+    prob = make_problem("adjoint_n16_k3", N=64, K=16, P=4, I=1, T=1, seed=29)
     with pytest.raises(capi.CalibError) as e:
         Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
                    n_intervals=prob["I"], samples=prob["T"], formulation=capi.CALIB_FORM_STATISTICS)
     assert e.value.code == capi.CALIB_EINVAL and "CALIB_FORM_DIRECT" in str(e.value)
+    cal = Calibrator(prob["N"], prob["pq"], prob["K"], prob["freqs"], prob["basis"], prob["rho"],
+                     n_intervals=prob["I"], samples=prob["T"], formulation=capi.CALIB_FORM_DIRECT)
+    cal.close()
 
 
 def test_full_size_uneven_first_jupdate_sample(lib):
