@@ -47,6 +47,7 @@ UNIT = "vis*dir*iter/s"
 # source it was taken on (sha256 prefix of the kernel's .cu file), else reported as null.
 NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum of one full capture each (summaries in profiles/)
     ("stats_hessvec", "fa12258caf66"): 81.27e6,
+    ("stats_trial", "c93f6cd6f93a"): 181.2e6,
     ("stats_pass", "532c6d147726"): 595.5e6,
     ("residual", "532c6d147726"): 615.2e6,
 }
@@ -395,7 +396,8 @@ def run_ours(args, world, rank, local):
             if v["launches"] and v["bytes_per_launch"] else None,
             "TFLOPs": v["flops_per_launch"] / (v["total_ms"] / 1e3 / v["launches"]) / 1e12
             if v["launches"] and v["flops_per_launch"] else None,
-            "share_of_step": v["total_ms"] / 1e3 / dt if dt else None}
+            "share_of_step": v["total_ms"] / 1e3 / dt if dt else None,
+            "traffic": NCU_TRAFFIC.get((k, source_hash(k))) if k in KERNEL_SOURCE else None}
         for k, v in prof.items()}
 
     # coherency prediction (once per step), after the timed region

@@ -99,7 +99,7 @@ typedef struct {
                                           the (agent, diagonal) items; 0 = automatic */
     int jupdate;                       /* CALIB_JUPDATE_LM (default), CALIB_JUPDATE_RTR or CALIB_JUPDATE_SAGE */
     int n_sage;                        /* SAGE sweeps per J-update (default 1; CALIB_JUPDATE_SAGE only) */
-    int freq_groups;                   /* G >= 1 (default 1), dividing P: frequency multiplexing. With more
+    int freq_groups;                   /* G >= 1 (default 1; 0 is taken as 1), dividing P: frequency multiplexing. With more
                                           frequencies than agents per consensus problem (Section 3), each
                                           interval's P frequencies form G interleaved subsets - subset g is
                                           the frequency indices g, g+G, g+2G, ... (each spans the band) -

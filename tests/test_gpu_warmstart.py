@@ -118,4 +118,8 @@ def test_warm_starts_reach_the_cold_residual_sooner(small_sequence):
     for name in ("previous", "network"):
         assert res[name]["reached"] == res[name]["of"]
         assert res[name]["iters_max"] <= res["plain"]["iters"]
+    # the network's start is kept only where it lowers L_i, so the summed starting objective is never
+    # higher; on this sequence it also starts closer to the target data cost
+    assert res["network"]["start_objective"] <= res["previous"]["start_objective"] * (1 + 1e-9)
+    assert res["network"]["start_data_cost_over_target"] < res["previous"]["start_data_cost_over_target"]
     net.close()
