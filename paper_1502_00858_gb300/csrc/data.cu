@@ -204,47 +204,31 @@ __global__ void __launch_bounds__(256) k_predict(const PredictArgs a, int s_chun
             E[((size_t)k * s_chunk + s) * N + p] = make_float2(cs, -sn);  // exp(-2 pi i turns)
         }
         __syncthreads();
-        // One thread per (diagonal, slot) with all K directions: consecutive threads read
-        // consecutive stations' phasors (no bank conflicts) and write consecutive K-vectors.
-        const int npad_max = (N + 3) / 4 * 4;
-        for (int it = threadIdx.x; it < a.D * npad_max; it += blockDim.x) {
-            const int d = it / npad_max, g = it - d * npad_max;
+        for (int d = 0; d < a.D; ++d) {
             const DiagDesc dsc = dsc_agent[d];
-            if (g >= dsc.n_pad) continue;
-            float2* out = a.C + dsc.coff + ((size_t)t * dsc.n_pad + g) * K;
-            int p = 0, q = 0;
-            const bool on = g < dsc.n;
-            if (on) {
-                const int sl = a.slot[dsc.slot_off + g];
-                p = sl & 0xff;
-                q = (sl >> 8) & 0xff;
-            }
-            float2 c[MAX_K];  // the K directions' sums, independent chains
-#pragma unroll
-            for (int k = 0; k < MAX_K; ++k) c[k] = make_float2(0.f, 0.f);
-            if (on) {
-                for (int s = 0; s < ns; ++s) {
-#pragma unroll
-                    for (int k = 0; k < MAX_K; ++k) {
-                        if (k >= K) continue;
-                        const float2 ep = E[((size_t)k * s_chunk + s) * N + p], eq = E[((size_t)k * s_chunk + s) * N + q];
+            float2* out = a.C + dsc.coff + (size_t)t * dsc.n_pad * K;
+            for (int it = threadIdx.x; it < dsc.n_pad * K; it += blockDim.x) {
+                const int g = it / K, k = it - g * K;
+                float2 c = make_float2(0.f, 0.f);
+                if (g < dsc.n) {
+                    const int sl = a.slot[dsc.slot_off + g];
+                    const int p = sl & 0xff, q = (sl >> 8) & 0xff;
+                    const float2* Ek = E + (size_t)k * s_chunk * N;
+                    const float* fk = flux + k * s_chunk;
+                    for (int s = 0; s < ns; ++s) {
+                        const float2 ep = Ek[s * N + p], eq = Ek[s * N + q];
                         // I_s E_p conj(E_q)
                         const float re = ep.x * eq.x + ep.y * eq.y;
                         const float im = ep.y * eq.x - ep.x * eq.y;
-                        const float fl = flux[k * s_chunk + s];
-                        c[k].x = fmaf(fl, re, c[k].x);
-                        c[k].y = fmaf(fl, im, c[k].y);
+                        c.x = fmaf(fk[s], re, c.x);
+                        c.y = fmaf(fk[s], im, c.y);
                     }
                 }
-            }
-#pragma unroll
-            for (int k = 0; k < MAX_K; ++k) {
-                if (k >= K) continue;
                 if (s0 == 0) {
-                    out[k] = c[k];
+                    out[it] = c;
                 } else {
-                    const float2 o = out[k];
-                    out[k] = make_float2(o.x + c[k].x, o.y + c[k].y);
+                    const float2 o = out[it];
+                    out[it] = make_float2(o.x + c.x, o.y + c.y);
                 }
             }
         }
