@@ -41,6 +41,32 @@ constexpr int MAX_N = 256;
 constexpr int MAX_K = 16;
 constexpr int MAX_M = 16;
 
+// Programmatic dependent launch (the kernel chain of the LM J-update). A kernel launched by
+// launch_k with pdl set may start while the preceding kernel in the stream is still running. It
+// executes griddep_wait() before it reads anything that kernel writes and before it writes anything
+// that kernel reads or writes; the wait returns once the preceding kernel has completed and its
+// memory is visible. It calls griddep_launch_dependents() only after its own wait, so a kernel that
+// starts early can rely on every kernel before its immediate predecessor having completed. Launched
+// without the attribute, both instructions return at once.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_k(bool pdl, void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl ? 1 : 0;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, args...);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 // Budget of a bounded in-kernel wait, in SM clock cycles (about one second at 2 GHz).
 constexpr long long WAIT_BUDGET_CYCLES = 2000000000LL;
 
@@ -105,6 +131,7 @@ struct LMArgs {
     double tau;
     int cost_from_decrease;  // trial cost g(J') = g(J) - decrease (statistics sweeps carry no cost)
     int timing;              // autotuner: PCG step runs its whole path and writes no agent state
+    int pdl;                 // launch with programmatic dependent launch (griddep_wait below)
 };
 
 struct ConsArgs {
@@ -214,6 +241,8 @@ struct SSArgs {
     float* part; double* part_dcost; int* status;
     int A, N, K, D, NP;
     int part_stride;   // pieces per agent in part / part_dcost (>= the CTAs meeting any one agent)
+    int pdl;           // launch with programmatic dependent launch; the statistics must not be
+                       // written by the preceding kernel (they are read before griddep_wait)
 };
 // grid CTAs split the A*D (agent, diagonal) items into equal contiguous ranges; 1 <= grid <= A*D.
 cudaError_t launch_ss_sweep(const SSArgs& a, bool hessvec, int grid, cudaStream_t s);

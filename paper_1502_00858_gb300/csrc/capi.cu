@@ -581,13 +581,15 @@ struct Enq {
         ok(c->jupdate == CALIB_JUPDATE_RTR ? launch_rtr_eval(la, mode, c->stream) : launch_lm_eval(la, mode, c->stream));
         end(pp);
     }
-    void sweep(int mode, const float* J, const float* eta) {
+    void sweep(int mode, const float* J, const float* eta, bool pdl = false) {
         const bool ss = c->formulation == 0 && mode != SWEEP_RESIDUAL;
         ProfPair pp = begin(ss ? (mode == SWEEP_HESSVEC ? 2 : 3) : (mode == SWEEP_HESSVEC ? 1 : 0));
         if (ss) {  // the statistics trial pass takes the trial point J' itself (written by the last PCG step)
             const float* e2 = mode == SWEEP_HESSVEC ? eta : c->Jt;
             const bool hv = mode == SWEEP_HESSVEC;
-            ok(launch_ss_sweep(ss_args(c, J, e2, hv), hv, hv ? c->part_hv.grid : c->part_tr.grid, c->stream));
+            SSArgs sa = ss_args(c, J, e2, hv);
+            sa.pdl = pdl ? 1 : 0;
+            ok(launch_ss_sweep(sa, hv, hv ? c->part_hv.grid : c->part_tr.grid, c->stream));
         } else {
             ok(launch_sweep(sweep_args(c, mode, J, eta), mode, c->stream));
         }
@@ -635,21 +637,27 @@ void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
         return;
     }
     const bool ssf = c->formulation == 0;
-    const LMArgs la_hv = lm_args(c, ssf ? PARTS_SS_HESSIAN : PARTS_DIRECT);  // after a Hessian sweep
-    const LMArgs la = lm_args(c, ssf ? PARTS_SS_TRIAL : PARTS_DIRECT);       // after the trial sweep
+    // Programmatic dependent launch through the LM chain (each kernel's prologue overlaps the tail of
+    // the one before); not with per-kernel profiling events, whose records sit between the kernels.
+    const bool pdl = c->jupdate == CALIB_JUPDATE_LM && !c->profiling;
+    LMArgs la_hv = lm_args(c, ssf ? PARTS_SS_HESSIAN : PARTS_DIRECT);  // after a Hessian sweep
+    LMArgs la = lm_args(c, ssf ? PARTS_SS_TRIAL : PARTS_DIRECT);       // after the trial sweep
+    la_hv.pdl = la.pdl = pdl ? 1 : 0;
     const ConsArgs ca = cons_args(c);
     if (eval_first) {  // the residual sweep is the direct one in both formulations (it yields g exactly)
         q.sweep(SWEEP_RESIDUAL, c->J, nullptr);
-        q.lm_eval(lm_args(c, PARTS_DIRECT), LM_BEGIN_FROM_PARTIALS);
+        LMArgs l0 = lm_args(c, PARTS_DIRECT);
+        l0.pdl = la.pdl;
+        q.lm_eval(l0, LM_BEGIN_FROM_PARTIALS);
     } else {
         q.lm_eval(la, LM_BEGIN_REUSE);
     }
     for (int l = 0; l < c->n_lm; ++l) {
         for (int k = 0; k < c->n_cg; ++k) {
-            q.sweep(SWEEP_HESSVEC, c->J, c->p);
+            q.sweep(SWEEP_HESSVEC, c->J, c->p, pdl);
             q.cg_step(la_hv, k == c->n_cg - 1);  // the last one forms the trial point
         }
-        q.sweep(SWEEP_TRIAL, c->J, c->x);
+        q.sweep(SWEEP_TRIAL, c->J, c->x, pdl);
         q.lm_eval(la, LM_ACCEPT);
     }
     ProfPair pp = q.begin(7);

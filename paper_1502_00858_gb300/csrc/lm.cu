@@ -357,6 +357,8 @@ __global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_lm_eval(co
     const int N = a.N, K = a.K, KN = K * N;
     const size_t off = (size_t)agent * KN * 8;
     AgentState& st = a.st[agent];
+    griddep_wait();  // the preceding kernel (a sweep or the fusion-centre step) writes what follows reads
+    griddep_launch_dependents();
 
     Blk j[BPT], y[BPT], bz[BPT], gg[BPT];
     float rk[BPT];
@@ -522,7 +524,9 @@ __global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_cg_step(co
     const int N = a.N, KN = a.K * N;
     const size_t off = (size_t)agent * KN * 8;
     AgentState& st = a.st[agent];
-    // Every load first, independent of the stop flag, so that they are in flight together.
+    // Every load first, independent of the stop flag, so that they are in flight together. The
+    // preceding kernel is the Hessian pass, which writes only the partials: the PCG vectors, the
+    // Jacobi blocks and the agent state are read before the dependency wait.
     Blk x[BPT], r[BPT], p[BPT], ap[BPT];  // ap holds the Hessian partial sum until it becomes A p
     float lam[BPT], G[BPT][4];
 #pragma unroll
@@ -535,7 +539,6 @@ __global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_cg_step(co
         x[i] = ld_blk(a.x + off, blk);
         r[i] = ld_blk(a.r + off, blk);
         p[i] = ld_blk(a.p + off, blk);
-        ap[i] = sum_parts(a, agent, blk, KN);
         const float4 q = reinterpret_cast<const float4*>(a.Gm + (size_t)agent * KN * 4)[blk];
         G[i][0] = q.x; G[i][1] = q.y; G[i][2] = q.z; G[i][3] = q.w;
         lam[i] = 0.5f * a.rho[blk / N];
@@ -543,6 +546,13 @@ __global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_cg_step(co
     const int stop = a.timing ? 0 : st.cg_stop;
     const float mu = a.timing ? 1.f : (float)st.mu;
     const float rz = a.timing ? 1.f : (float)st.rz;
+    griddep_wait();
+    griddep_launch_dependents();
+#pragma unroll
+    for (int i = 0; i < BPT; ++i) {
+        const int blk = tid + i * T;
+        if (blk < KN) ap[i] = sum_parts(a, agent, blk, KN);
+    }
     if (!stop) {
         float v[1] = {0.f};
 #pragma unroll
@@ -948,13 +958,11 @@ LMShape lm_shape(int KN) {
 template <int BPT>
 cudaError_t eval_go(const LMArgs& a, int mode, int threads, cudaStream_t s) {
     const size_t smem = (size_t)a.K * a.N * GT * sizeof(float);
-    k_lm_eval<BPT><<<a.A, threads, smem, s>>>(a, mode);
-    return cudaGetLastError();
+    return launch_k(a.pdl != 0, k_lm_eval<BPT>, a.A, threads, smem, s, a, mode);
 }
 template <int BPT>
 cudaError_t cg_go(const LMArgs& a, bool last, int threads, cudaStream_t s) {
-    k_cg_step<BPT><<<a.A, threads, 0, s>>>(a, last ? 1 : 0);
-    return cudaGetLastError();
+    return launch_k(a.pdl != 0, k_cg_step<BPT>, a.A, threads, 0, s, a, last ? 1 : 0);
 }
 template <int BPT>
 cudaError_t rtr_eval_go(const LMArgs& a, int mode, int threads, cudaStream_t s) {

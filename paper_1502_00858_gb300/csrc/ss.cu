@@ -93,6 +93,10 @@ __global__ void __launch_bounds__(SMALL ? 128 : 256,
     };
     if (tid == 0)
         for (int s2 = 0; s2 < min(NST - 1, S); ++s2) issue(s2);
+    // Everything above reads only the statistics; J, eta (or J') and the partial buffers belong to
+    // the preceding kernels of the chain (programmatic dependent launch).
+    griddep_wait();
+    griddep_launch_dependents();
 
     float4 Jf[KB], Ef[KB], A1[KB];  // rows rr of station g's J and eta / J'; its first-station sums
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -333,16 +337,11 @@ cudaError_t prep_all() {
 
 template <int KB, bool HV>
 cudaError_t go(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
-    const bool exact = a.K == KB, small = threads <= 128;
-    if (exact && small)
-        k_ss_sweep<KB, HV, true, true><<<grid, threads, smem, s>>>(a, sb);
-    else if (exact)
-        k_ss_sweep<KB, HV, true, false><<<grid, threads, smem, s>>>(a, sb);
-    else if (small)
-        k_ss_sweep<KB, HV, false, true><<<grid, threads, smem, s>>>(a, sb);
-    else
-        k_ss_sweep<KB, HV, false, false><<<grid, threads, smem, s>>>(a, sb);
-    return cudaGetLastError();
+    const bool exact = a.K == KB, small = threads <= 128, pdl = a.pdl != 0;
+    if (exact && small) return launch_k(pdl, k_ss_sweep<KB, HV, true, true>, grid, threads, smem, s, a, sb);
+    if (exact) return launch_k(pdl, k_ss_sweep<KB, HV, true, false>, grid, threads, smem, s, a, sb);
+    if (small) return launch_k(pdl, k_ss_sweep<KB, HV, false, true>, grid, threads, smem, s, a, sb);
+    return launch_k(pdl, k_ss_sweep<KB, HV, false, false>, grid, threads, smem, s, a, sb);
 }
 template <bool HV>
 cudaError_t dispatch(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {

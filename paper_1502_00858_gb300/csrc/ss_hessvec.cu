@@ -59,6 +59,10 @@ __global__ void __launch_bounds__(128, 2) k_ss_hessvec(const SSArgs a, const int
     };
     if (tid == 0)
         for (int s2 = 0; s2 < min(NST - 1, S); ++s2) issue(s2);
+    // Everything above reads only the statistics; J, eta (or J') and the partial buffers belong to
+    // the preceding kernels of the chain (programmatic dependent launch).
+    griddep_wait();
+    griddep_launch_dependents();
 
     float4 Jf[KB][2], Ef[KB][2], A1[KB][2];  // station g's rows of J and eta; its first-station sums
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -217,8 +221,7 @@ cudaError_t prep_hv1() {
 
 template <int KB>
 cudaError_t go_hv1(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
-    k_ss_hessvec<KB><<<grid, threads, smem, s>>>(a, sb);
-    return cudaGetLastError();
+    return launch_k(a.pdl != 0, k_ss_hessvec<KB>, grid, threads, smem, s, a, sb);
 }
 
 cudaError_t dispatch_hv1(const SSArgs& a, int grid, int threads, size_t smem, int sb, cudaStream_t s) {
