@@ -134,6 +134,9 @@ struct LMArgs {
     int pdl;                 // launch with programmatic dependent launch (griddep_wait below)
 };
 
+// Z-update CTAs per (consensus problem, direction) at most: 32 (station, entry) positions each, N <= 128.
+constexpr int Z_SLOTS = 32;
+
 struct ConsArgs {
     float* J; float* gradg; float* Gm; float* Y; float* BZ;
     double* Z; double* Zprev;
@@ -142,7 +145,7 @@ struct ConsArgs {
     const float* rho;       // [K]
     AgentState* st;
     double* prim;           // [A][K] ||J_ik - B_i Z_k||
-    double* dual2;          // [I][K][8] per-CTA shares of ||Z_k^{n+1} - Z_k^n||^2
+    double* dual2;          // [I * G][K][Z_SLOTS] per-CTA shares of ||Z_k^{n+1} - Z_k^n||^2
     double* stats;          // [max_iters][4]
     int* iter_counter;
     // Consensus problems: each of the I intervals' P frequencies splits into G interleaved groups

@@ -956,7 +956,7 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     okm = okm && dalloc(&c->basis_d, (size_t)P * M) == cudaSuccess && dalloc(&c->Pinv_d, (size_t)c->G * M * M) == cudaSuccess;
     okm = okm && dalloc(&c->freqs_d, (size_t)P) == cudaSuccess && dalloc(&c->rho_d, (size_t)K) == cudaSuccess;
     okm = okm && dalloc(&c->st, (size_t)A) == cudaSuccess && dalloc(&c->prim, (size_t)A * K) == cudaSuccess;
-    okm = okm && dalloc(&c->dual2, (size_t)c->I * c->G * K * 8) == cudaSuccess;
+    okm = okm && dalloc(&c->dual2, (size_t)c->I * c->G * K * Z_SLOTS) == cudaSuccess;
     okm = okm && dalloc(&c->iter_counter, 1) == cudaSuccess && dalloc(&c->status, 1) == cudaSuccess;
     okm = okm && dalloc(&c->evL, (size_t)A) == cudaSuccess && dalloc(&c->evG, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess && dalloc(&c->part_hv.pn, (size_t)A) == cudaSuccess &&

@@ -115,31 +115,33 @@ __global__ void __launch_bounds__(CT) k_gauge(const ConsArgs a) {
 }
 
 // Z_k = (1/rho_k) Pinv (sum_f b(f) (Y_fk + rho_k J_fk)) per interval, direction, station and entry
-// (Eq. Zest in the reshaped form z = vec(R P^T) of Section 3): one thread per (interval, direction,
-// station, entry), ZT of them per CTA; float64 accumulation over the P agents (frequencies). Also
+// (Eq. Zest in the reshaped form z = vec(R P^T) of Section 3). A CTA takes ZJ consecutive (station,
+// entry) positions of one (consensus problem, direction); its ZG warps split the problem's agents
+// (warp w takes the agents w, w + ZG, ...) and accumulate R = sum_f b(f) (Y + rho J) in float64, and
+// the warps' sums are added in warp order (a fixed order: results do not depend on timing). Also
 // this CTA's share of ||Z_k^{n+1} - Z_k^n||^2 for the dual residual (Section 4), written to its own
 // slot and summed in a fixed order by k_stats.
-constexpr int ZT = 128;
-constexpr int ZSLOTS = 8;  // CTAs per (interval, direction): 8N / ZT <= 8 for N <= 128
+constexpr int ZJ = 32;  // (station, entry) positions per CTA: one per lane
+constexpr int ZG = 4;   // warps per CTA, each over every ZG-th agent of the problem
 
-__global__ void __launch_bounds__(ZT) k_zupdate(const ConsArgs a) {
+__global__ void __launch_bounds__(ZJ * ZG) k_zupdate(const ConsArgs a) {
+    __shared__ double Rs[ZG - 1][MAX_M][ZJ];
     __shared__ double red[33];
     const int ivk = blockIdx.x;  // (consensus problem, direction)
     const int k = ivk % a.K, pb = ivk / a.K;
     const int iv = pb / a.G, g = pb - iv * a.G, Pg = a.P / a.G;
-    const int j = blockIdx.y * ZT + threadIdx.x;  // (station, entry) = (j / 8, j % 8)
+    const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    const int j = blockIdx.y * ZJ + lane;  // (station, entry) = (j / 8, j % 8)
     const int NE = a.N * 8, M = a.M;
     const double rk = a.rho[k];
-    const double* Pinv = a.Pinv + (size_t)g * M * M;
-    double dz2 = 0.0;
-    if (j < NE) {
-        double R[MAX_M];
+    double R[MAX_M];
 #pragma unroll
-        for (int l = 0; l < MAX_M; ++l) R[l] = 0.0;
+    for (int l = 0; l < MAX_M; ++l) R[l] = 0.0;
+    if (j < NE) {
         const size_t stride = (size_t)a.G * a.K * NE;  // next agent of the problem, same direction
         const size_t o0 = (((size_t)iv * a.P + g) * a.K + k) * NE + j;
 #pragma unroll 4
-        for (int jj = 0; jj < Pg; ++jj) {
+        for (int jj = grp; jj < Pg; jj += ZG) {
             const size_t o = o0 + (size_t)jj * stride;
             const double v = (double)__ldg(a.Y + o) + rk * (double)__ldg(a.J + o);
             const double* bf = a.basis + (size_t)(g + a.G * jj) * M;
@@ -147,6 +149,21 @@ __global__ void __launch_bounds__(ZT) k_zupdate(const ConsArgs a) {
             for (int l = 0; l < MAX_M; ++l)
                 if (l < M) R[l] = fma(__ldg(bf + l), v, R[l]);
         }
+    }
+    if (grp > 0) {
+#pragma unroll
+        for (int l = 0; l < MAX_M; ++l)
+            if (l < M) Rs[grp - 1][l][lane] = R[l];
+    }
+    __syncthreads();
+    double dz2 = 0.0;
+    if (grp == 0 && j < NE) {
+#pragma unroll
+        for (int w = 0; w < ZG - 1; ++w)
+#pragma unroll
+            for (int l = 0; l < MAX_M; ++l)
+                if (l < M) R[l] += Rs[w][l][lane];
+        const double* Pinv = a.Pinv + (size_t)g * M * M;
 #pragma unroll
         for (int l = 0; l < MAX_M; ++l) {
             if (l >= M) continue;
@@ -163,7 +180,7 @@ __global__ void __launch_bounds__(ZT) k_zupdate(const ConsArgs a) {
         }
     }
     dz2 = bsum(dz2, red);
-    if (threadIdx.x == 0) a.dual2[(size_t)ivk * ZSLOTS + blockIdx.y] = dz2;
+    if (threadIdx.x == 0) a.dual2[(size_t)ivk * Z_SLOTS + blockIdx.y] = dz2;
 }
 
 // BZ_i = sum_l b_l(f_i) Z_l; Y_i += rho (J_i - BZ_i) (Eq. M3); per-agent ||J_ik - BZ_ik|| and
@@ -181,11 +198,13 @@ __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) 
     double bl[MAX_M];
 #pragma unroll
     for (int l = 0; l < MAX_M; ++l) bl[l] = l < M ? a.basis[f * M + l] : 0.0;
-    double pen = 0.0;
+    // B Z, the difference J - B Z and the new Y in float64; the squares and the penalty terms of
+    // that difference (records only) in float32, summed in float64 across the CTA.
+    float pen = 0.f;
     const int KN8r = (KN8 + blockDim.x - 1) / blockDim.x * blockDim.x;  // every lane runs every trip
     for (int i = threadIdx.x; i < KN8r; i += blockDim.x) {
         const bool on = i < KN8;  // KN8 is a multiple of 8: a block's 8 lanes are all on or all off
-        double dd = 0.0;
+        float dd = 0.f;
         if (on) {
             const int k = i / (N * 8), pe = i - k * N * 8;  // pe = station * 8 + entry
             const double rk = a.rho[k];
@@ -199,13 +218,14 @@ __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) 
             const float ynew = update_y ? (float)((double)a.Y[o] + rk * d) : a.Y[o];
             a.Y[o] = ynew;
             a.BZ[o] = (float)bz;
-            dd = d * d;
-            pen += (double)ynew * d + 0.5 * rk * d * d;
+            const float df = (float)d, rf = a.rho[k];
+            dd = df * df;
+            pen += fmaf(ynew, df, 0.5f * rf * dd);
         }
         for (int w = 4; w > 0; w >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, w);
-        if (on && (i & 7) == 0) dds[i >> 3] = dd;
+        if (on && (i & 7) == 0) dds[i >> 3] = (double)dd;
     }
-    pen = bsum(pen, red);  // its barriers also publish dds
+    const double pen_d = bsum((double)pen, red);  // its barriers also publish dds
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int k = warp; k < a.K; k += nw) {
         double s = 0.0;
@@ -213,7 +233,7 @@ __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) 
         for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
         if (lane == 0 && a.prim) a.prim[(size_t)agent * a.K + k] = sqrt(s);
     }
-    if (threadIdx.x == 0) a.st[agent].L = a.st[agent].g + pen;
+    if (threadIdx.x == 0) a.st[agent].L = a.st[agent].g + pen_d;
 }
 
 // Per-iteration record (Section 4): primal, dual, objective, data residual norm.
@@ -221,10 +241,10 @@ __global__ void __launch_bounds__(CT) k_stats(const ConsArgs a) {
     __shared__ double red[33];
     double prim = 0.0, dual = 0.0, obj = 0.0, g = 0.0;
     for (int i = threadIdx.x; i < a.A * a.K; i += blockDim.x) prim += a.prim[i];
-    const int zs = (a.N * 8 + ZT - 1) / ZT;  // Z-update CTAs per (interval, direction)
+    const int zs = (a.N * 8 + ZJ - 1) / ZJ;  // Z-update CTAs per (consensus problem, direction)
     for (int i = threadIdx.x; i < a.I * a.G * a.K; i += blockDim.x) {
         double d2 = 0.0;
-        for (int y = 0; y < zs; ++y) d2 += a.dual2[(size_t)i * ZSLOTS + y];
+        for (int y = 0; y < zs; ++y) d2 += a.dual2[(size_t)i * Z_SLOTS + y];
         dual += sqrt(d2);
     }
     for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
@@ -263,9 +283,9 @@ cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 cudaError_t launch_zupdate(const ConsArgs& a, cudaStream_t s) {
-    const int zs = (a.N * 8 + ZT - 1) / ZT;
-    if (zs > ZSLOTS || a.M > MAX_M) return cudaErrorInvalidConfiguration;
-    k_zupdate<<<dim3(a.I * a.G * a.K, zs), ZT, 0, s>>>(a);
+    const int zs = (a.N * 8 + ZJ - 1) / ZJ;
+    if (zs > Z_SLOTS || a.M > MAX_M) return cudaErrorInvalidConfiguration;
+    k_zupdate<<<dim3(a.I * a.G * a.K, zs), ZJ * ZG, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_yupdate(const ConsArgs& a, cudaStream_t s) {

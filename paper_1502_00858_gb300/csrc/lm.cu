@@ -357,33 +357,33 @@ __global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_lm_eval(co
     const int N = a.N, K = a.K, KN = K * N;
     const size_t off = (size_t)agent * KN * 8;
     AgentState& st = a.st[agent];
-    griddep_wait();  // the preceding kernel (a sweep or the fusion-centre step) writes what follows reads
-    griddep_launch_dependents();
 
-    Blk j[BPT], y[BPT], bz[BPT], gg[BPT];
+    // J, Y, BZ and J' are read before the dependency wait: the preceding kernel (a residual or
+    // trial sweep, or the fusion-centre step's record kernel) writes only partials and records.
+    Blk j[BPT], y[BPT], bz[BPT], gg[BPT], jt[BPT];
     float rk[BPT];
 #pragma unroll
     for (int i = 0; i < BPT; ++i) {
         const int blk = tid + i * T;
-        j[i] = y[i] = bz[i] = gg[i] = zero_blk();
+        j[i] = y[i] = bz[i] = gg[i] = jt[i] = zero_blk();
         rk[i] = 0.f;
         if (blk < KN) {
             j[i] = ld_blk(a.J + off, blk);
             y[i] = ld_blk(a.Y + off, blk);
             bz[i] = ld_blk(a.BZ + off, blk);
+            if (mode == LM_ACCEPT) jt[i] = ld_blk(a.Jt + off, blk);
             rk[i] = a.rho[blk / N];
         }
     }
+    griddep_wait();
+    griddep_launch_dependents();
     bool fresh = false;  // gradg re-formed from the sweep's partials: project it and rebuild G
     if (mode == LM_ACCEPT) {  // the trial sweep just ran at Jt = J + x
-        Blk jt[BPT];
         float v[2] = {0.f, 0.f};
 #pragma unroll
         for (int i = 0; i < BPT; ++i) {
             const int blk = tid + i * T;
-            jt[i] = zero_blk();
             if (blk < KN) {
-                jt[i] = ld_blk(a.Jt + off, blk);
                 v[0] += penalty_blk(jt[i], y[i], bz[i], rk[i]);
                 v[1] += penalty_decrease_blk(j[i], jt[i], y[i], bz[i], rk[i]);
             }
