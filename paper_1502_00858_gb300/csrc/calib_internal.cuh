@@ -136,6 +136,8 @@ struct LMArgs {
 
 // Z-update CTAs per (consensus problem, direction) at most: 32 (station, entry) positions each, N <= 128.
 constexpr int Z_SLOTS = 32;
+// Agents per CTA of the per-iteration record kernel (one warp each).
+constexpr int REC_AGENTS = 8;
 
 struct ConsArgs {
     float* J; float* gradg; float* Gm; float* Y; float* BZ;
@@ -146,6 +148,13 @@ struct ConsArgs {
     AgentState* st;
     double* prim;           // [A][K] ||J_ik - B_i Z_k||
     double* dual2;          // [I * G][K][Z_SLOTS] per-CTA shares of ||Z_k^{n+1} - Z_k^n||^2
+    const float2* basis_df; // [P][M] the basis as double-float (hi, lo) pairs
+    const float2* Pinv_df;  // [G][M][M] Pinv as double-float pairs
+    const float2* rinv_df;  // [K] 1 / rho_k as double-float pairs
+    float* prim_part;       // [A][K][Z_SLOTS] per-CTA shares of ||J_ik - B_i Z_k||^2
+    float* pen_part;        // [A][K][Z_SLOTS] per-CTA shares of Re tr(Y^H D) + rho/2 ||D||^2, D = J - B Z
+    double* rec_part;       // [ceil(A / REC_AGENTS)][3] per-CTA sums of the record kernel
+    int* rec_count;         // record-kernel CTAs done in the current launch (0 between launches)
     double* stats;          // [max_iters][4]
     int* iter_counter;
     // Consensus problems: each of the I intervals' P frequencies splits into G interleaved groups
@@ -191,9 +200,10 @@ cudaError_t launch_sage_scatter(const SageArgs& g, int k, cudaStream_t s);
 
 // ---- launchers (consensus.cu)
 cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s);
-cudaError_t launch_zupdate(const ConsArgs& a, cudaStream_t s);
-cudaError_t launch_yupdate(const ConsArgs& a, cudaStream_t s);
-cudaError_t launch_stats(const ConsArgs& a, cudaStream_t s);
+// Z-update (Eq. Zest) and Y-update (Eq. M3) of one C-ADMM iteration in one launch, then the
+// iteration's records (Section 4) and each agent's L_i.
+cudaError_t launch_zy_update(const ConsArgs& a, cudaStream_t s);
+cudaError_t launch_records(const ConsArgs& a, cudaStream_t s);
 cudaError_t launch_bz_only(const ConsArgs& a, cudaStream_t s);
 cudaError_t launch_identity(float* J, long long n_blocks, cudaStream_t s);
 

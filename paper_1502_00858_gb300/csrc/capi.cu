@@ -12,6 +12,7 @@
 
 #include "calib.h"
 #include "calib_internal.cuh"
+#include "df.cuh"
 #include "tma.cuh"
 
 namespace calib {
@@ -132,6 +133,10 @@ struct calib_ctx {
     AgentState* st = nullptr;
     double* prim = nullptr;
     double* dual2 = nullptr;
+    float2 *basis_df = nullptr, *Pinv_df = nullptr, *rinv_df = nullptr;  // double-float tables
+    float *prim_part = nullptr, *pen_part = nullptr;  // per-CTA shares of the fused Z/Y update
+    double* rec_part = nullptr;                       // per-CTA sums of the record kernel
+    int* rec_count = nullptr;
     double* stats = nullptr;
     int max_iters = 0;
     int* iter_counter = nullptr;
@@ -331,6 +336,13 @@ ConsArgs cons_args(calib_ctx* c) {
     a.st = c->st;
     a.prim = c->prim;
     a.dual2 = c->dual2;
+    a.basis_df = c->basis_df;
+    a.Pinv_df = c->Pinv_df;
+    a.rinv_df = c->rinv_df;
+    a.prim_part = c->prim_part;
+    a.pen_part = c->pen_part;
+    a.rec_part = c->rec_part;
+    a.rec_count = c->rec_count;
     a.stats = c->stats;
     a.iter_counter = c->iter_counter;
     a.A = c->A;
@@ -631,9 +643,8 @@ void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
         const ConsArgs ca = cons_args(c);
         enqueue_sage_jupdate(q);
         if (gauge) q.ok(launch_gauge(ca, c->stream));
-        q.ok(launch_zupdate(ca, c->stream));
-        q.ok(launch_yupdate(ca, c->stream));
-        q.ok(launch_stats(ca, c->stream));
+        q.ok(launch_zy_update(ca, c->stream));
+        q.ok(launch_records(ca, c->stream));
         return;
     }
     const bool ssf = c->formulation == 0;
@@ -662,9 +673,8 @@ void enqueue_iteration(Enq& q, bool eval_first, bool gauge) {
     }
     ProfPair pp = q.begin(7);
     if (gauge) q.ok(launch_gauge(ca, c->stream));
-    q.ok(launch_zupdate(ca, c->stream));
-    q.ok(launch_yupdate(ca, c->stream));
-    q.ok(launch_stats(ca, c->stream));
+    q.ok(launch_zy_update(ca, c->stream));
+    q.ok(launch_records(ca, c->stream));
     q.end(pp);
 }
 
@@ -957,6 +967,12 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     okm = okm && dalloc(&c->freqs_d, (size_t)P) == cudaSuccess && dalloc(&c->rho_d, (size_t)K) == cudaSuccess;
     okm = okm && dalloc(&c->st, (size_t)A) == cudaSuccess && dalloc(&c->prim, (size_t)A * K) == cudaSuccess;
     okm = okm && dalloc(&c->dual2, (size_t)c->I * c->G * K * Z_SLOTS) == cudaSuccess;
+    okm = okm && dalloc(&c->basis_df, (size_t)P * M) == cudaSuccess && dalloc(&c->Pinv_df, (size_t)c->G * M * M) == cudaSuccess &&
+          dalloc(&c->rinv_df, (size_t)K) == cudaSuccess;
+    okm = okm && dalloc(&c->prim_part, (size_t)A * K * Z_SLOTS) == cudaSuccess &&
+          dalloc(&c->pen_part, (size_t)A * K * Z_SLOTS) == cudaSuccess;
+    okm = okm && dalloc(&c->rec_part, (size_t)(A + REC_AGENTS - 1) / REC_AGENTS * 3) == cudaSuccess &&
+          dalloc(&c->rec_count, 1) == cudaSuccess;
     okm = okm && dalloc(&c->iter_counter, 1) == cudaSuccess && dalloc(&c->status, 1) == cudaSuccess;
     okm = okm && dalloc(&c->evL, (size_t)A) == cudaSuccess && dalloc(&c->evG, (size_t)A) == cudaSuccess;
     okm = okm && dalloc(&c->T_d, (size_t)A) == cudaSuccess && dalloc(&c->part_hv.pn, (size_t)A) == cudaSuccess &&
@@ -974,6 +990,16 @@ int calib_init(calib_ctx** out, int n_stations, int n_baselines, const int32_t* 
     if (ensure_stats(c, 64) != CALIB_OK) return bail(CALIB_ENOMEM);
     cudaMemcpy(c->basis_d, c->basis.data(), c->basis.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(c->Pinv_d, c->Pinv.data(), c->Pinv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    {
+        std::vector<float2> bdf(c->basis.size()), pdf(c->Pinv.size()), rdf(K);
+        for (size_t i = 0; i < bdf.size(); ++i) bdf[i] = df_split(c->basis[i]);
+        for (size_t i = 0; i < pdf.size(); ++i) pdf[i] = df_split(c->Pinv[i]);
+        for (int k = 0; k < K; ++k) rdf[k] = df_split(1.0 / (double)c->rho_f[k]);
+        cudaMemcpy(c->basis_df, bdf.data(), bdf.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->Pinv_df, pdf.data(), pdf.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        cudaMemcpy(c->rinv_df, rdf.data(), rdf.size() * sizeof(float2), cudaMemcpyHostToDevice);
+        cudaMemset(c->rec_count, 0, sizeof(int));
+    }
     cudaMemcpy(c->freqs_d, c->freqs.data(), c->freqs.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(c->rho_d, c->rho_f.data(), c->rho_f.size() * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(c->T_d, c->T.data(), c->T.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -1660,7 +1686,9 @@ void calib_destroy(calib_ctx* c) {
                     (void*)c->x, (void*)c->r, (void*)c->p, (void*)c->Gm,
                     (void*)c->evJ, (void*)c->evE, (void*)c->evOut, (void*)c->part, (void*)c->part_cost, (void*)c->part_dcost,
                     (void*)c->Z, (void*)c->Zprev, (void*)c->basis_d, (void*)c->Pinv_d, (void*)c->freqs_d,
-                    (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->dual2, (void*)c->stats, (void*)c->iter_counter,
+                    (void*)c->rho_d, (void*)c->st, (void*)c->prim, (void*)c->dual2,
+                    (void*)c->basis_df, (void*)c->Pinv_df, (void*)c->rinv_df, (void*)c->prim_part, (void*)c->pen_part,
+                    (void*)c->rec_part, (void*)c->rec_count, (void*)c->stats, (void*)c->iter_counter,
                     (void*)c->status, (void*)c->part_hv.pn, (void*)c->part_tr.pn, (void*)c->evL, (void*)c->evG, (void*)c->T_d, (void*)c->vis_off_d,
                     (void*)c->coh_off_d, c->staging, (void*)c->ws_prev, (void*)c->ws_mlp, (void*)c->ws_L,
                     (void*)c->xf_d, (void*)c->ws_chose, (void*)c->sgU, (void*)c->sgS, (void*)c->sgJ, (void*)c->sgJt,

@@ -5,6 +5,7 @@
 #include <math.h>
 
 #include "calib_internal.cuh"
+#include "df.cuh"
 
 namespace calib {
 namespace {
@@ -114,18 +115,24 @@ __global__ void __launch_bounds__(CT) k_gauge(const ConsArgs a) {
     (void)f;
 }
 
-// Z_k = (1/rho_k) Pinv (sum_f b(f) (Y_fk + rho_k J_fk)) per interval, direction, station and entry
-// (Eq. Zest in the reshaped form z = vec(R P^T) of Section 3). A CTA takes ZJ consecutive (station,
-// entry) positions of one (consensus problem, direction); its ZG warps split the problem's agents
-// (warp w takes the agents w, w + ZG, ...) and accumulate R = sum_f b(f) (Y + rho J) in float64, and
-// the warps' sums are added in warp order (a fixed order: results do not depend on timing). Also
-// this CTA's share of ||Z_k^{n+1} - Z_k^n||^2 for the dual residual (Section 4), written to its own
-// slot and summed in a fixed order by k_stats.
+// One C-ADMM fusion-centre and dual step for one (consensus problem, direction) and ZJ consecutive
+// (station, entry) positions, in double-float arithmetic (df.cuh; the GPU's float64 rate is far
+// below its float32 rate and this step has few bytes per operation):
+//   Z-update (Eq. Zest in the reshaped form z = vec(R P^T) of Section 3):
+//     Z_k = (1/rho_k) Pinv sum_f b(f) (Y_fk + rho_k J_fk); the ZG warps split the problem's agents
+//     (warp w takes the agents w, w + ZG, ...) and their sums are added in warp order (a fixed
+//     order: results do not depend on timing); Z, Zprev are stored in float64, and this CTA's share
+//     of ||Z_k^{n+1} - Z_k^n||^2 (the dual residual, Section 4) goes to its own slot of dual2;
+//   Y-update (Eq. M3) of every agent f of the problem at the same positions, from the new Z held in
+//     shared memory: B_f Z = sum_l b_l(f) Z_l, D = J_f - B_f Z, Y_f += rho_k D (rounded once to
+//     float32), and the agent's shares of ||D||^2 and of Re tr(Y^H D) + rho/2 ||D||^2 (Eq. sumtrace2,
+//     with the new Y) over these positions, in float32, summed by k_records.
 constexpr int ZJ = 32;  // (station, entry) positions per CTA: one per lane
 constexpr int ZG = 4;   // warps per CTA, each over every ZG-th agent of the problem
 
-__global__ void __launch_bounds__(ZJ * ZG) k_zupdate(const ConsArgs a) {
-    __shared__ double Rs[ZG - 1][MAX_M][ZJ];
+__global__ void __launch_bounds__(ZJ * ZG) k_zy_update(const ConsArgs a) {
+    __shared__ float2 Rs[ZG - 1][MAX_M][ZJ];
+    __shared__ float2 Zs[MAX_M][ZJ];
     __shared__ double red[33];
     const int ivk = blockIdx.x;  // (consensus problem, direction)
     const int k = ivk % a.K, pb = ivk / a.K;
@@ -133,62 +140,100 @@ __global__ void __launch_bounds__(ZJ * ZG) k_zupdate(const ConsArgs a) {
     const int lane = threadIdx.x & 31, grp = threadIdx.x >> 5;
     const int j = blockIdx.y * ZJ + lane;  // (station, entry) = (j / 8, j % 8)
     const int NE = a.N * 8, M = a.M;
-    const double rk = a.rho[k];
-    double R[MAX_M];
+    const bool on = j < NE;
+    const float rk = a.rho[k];
+    const size_t stride = (size_t)a.G * a.K * NE;  // next agent of the problem, same direction
+    const size_t o0 = (((size_t)iv * a.P + g) * a.K + k) * NE + j;
+    DF R[MAX_M];
 #pragma unroll
-    for (int l = 0; l < MAX_M; ++l) R[l] = 0.0;
-    if (j < NE) {
-        const size_t stride = (size_t)a.G * a.K * NE;  // next agent of the problem, same direction
-        const size_t o0 = (((size_t)iv * a.P + g) * a.K + k) * NE + j;
-#pragma unroll 4
+    for (int l = 0; l < MAX_M; ++l) R[l] = DF{0.f, 0.f};
+    if (on) {
+#pragma unroll 2
         for (int jj = grp; jj < Pg; jj += ZG) {
             const size_t o = o0 + (size_t)jj * stride;
-            const double v = (double)__ldg(a.Y + o) + rk * (double)__ldg(a.J + o);
-            const double* bf = a.basis + (size_t)(g + a.G * jj) * M;
+            const DF v = df_add(df_prod(rk, __ldg(a.J + o)), DF{__ldg(a.Y + o), 0.f});  // Y + rho J
+            const float2* bf = a.basis_df + (size_t)(g + a.G * jj) * M;
 #pragma unroll
             for (int l = 0; l < MAX_M; ++l)
-                if (l < M) R[l] = fma(__ldg(bf + l), v, R[l]);
+                if (l < M) R[l] = df_fma(df_load(bf + l), v, R[l]);
         }
     }
     if (grp > 0) {
 #pragma unroll
         for (int l = 0; l < MAX_M; ++l)
-            if (l < M) Rs[grp - 1][l][lane] = R[l];
+            if (l < M) Rs[grp - 1][l][lane] = make_float2(R[l].hi, R[l].lo);
     }
     __syncthreads();
     double dz2 = 0.0;
-    if (grp == 0 && j < NE) {
+    if (grp == 0 && on) {
 #pragma unroll
         for (int w = 0; w < ZG - 1; ++w)
 #pragma unroll
             for (int l = 0; l < MAX_M; ++l)
-                if (l < M) R[l] += Rs[w][l][lane];
-        const double* Pinv = a.Pinv + (size_t)g * M * M;
+                if (l < M) R[l] = df_add(R[l], df_load(&Rs[w][l][lane]));
+        const float2* Pinv = a.Pinv_df + (size_t)g * M * M;
+        const DF ri = df_load(a.rinv_df + k);
 #pragma unroll
         for (int l = 0; l < MAX_M; ++l) {
             if (l >= M) continue;
-            double z = 0.0;
+            DF z{0.f, 0.f};
 #pragma unroll
             for (int m = 0; m < MAX_M; ++m)
-                if (m < M) z = fma(__ldg(Pinv + l * M + m), R[m], z);
-            z /= rk;
+                if (m < M) z = df_fma(df_load(Pinv + l * M + m), R[m], z);
+            z = df_mul(z, ri);
             const size_t zo = (((size_t)pb * a.K + k) * M + l) * NE + j;
-            const double old = a.Z[zo];
+            const double zd = df_to_double(z), old = a.Z[zo];
             a.Zprev[zo] = old;
-            a.Z[zo] = z;
-            dz2 = fma(z - old, z - old, dz2);
+            a.Z[zo] = zd;
+            dz2 = fma(zd - old, zd - old, dz2);
+            Zs[l][lane] = make_float2(z.hi, z.lo);
         }
     }
-    dz2 = bsum(dz2, red);
+    dz2 = bsum(dz2, red);  // its barriers also publish Zs
     if (threadIdx.x == 0) a.dual2[(size_t)ivk * Z_SLOTS + blockIdx.y] = dz2;
+
+    DF zl[MAX_M];
+#pragma unroll
+    for (int l = 0; l < MAX_M; ++l) zl[l] = (on && l < M) ? df_load(&Zs[l][lane]) : DF{0.f, 0.f};
+    for (int jj = grp; jj < Pg; jj += ZG) {  // the same trip count in every lane of the warp
+        const int f = g + a.G * jj;
+        float dd = 0.f, pen = 0.f;
+        if (on) {
+            const size_t o = o0 + (size_t)jj * stride;
+            const float2* bf = a.basis_df + (size_t)f * M;
+            DF bz{0.f, 0.f};
+#pragma unroll
+            for (int l = 0; l < MAX_M; ++l)
+                if (l < M) bz = df_fma(df_load(bf + l), zl[l], bz);
+            const float y = a.Y[o];
+            const DF d = df_add(DF{a.J[o], 0.f}, df_neg(bz));  // J - B Z
+            DF t = df_prod(rk, d.hi);
+            t.lo = __fmaf_rn(rk, d.lo, t.lo);
+            const float ynew = df_add(t, DF{y, 0.f}).hi;  // Y + rho D
+            a.Y[o] = ynew;
+            a.BZ[o] = bz.hi;
+            dd = d.hi * d.hi;
+            pen = fmaf(ynew, d.hi, 0.5f * rk * dd);
+        }
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1) {
+            dd += __shfl_xor_sync(0xffffffffu, dd, w);
+            pen += __shfl_xor_sync(0xffffffffu, pen, w);
+        }
+        if (lane == 0) {
+            const size_t po = (((size_t)iv * a.P + f) * a.K + k) * Z_SLOTS + blockIdx.y;
+            a.prim_part[po] = dd;
+            a.pen_part[po] = pen;
+        }
+    }
 }
 
-// BZ_i = sum_l b_l(f_i) Z_l; Y_i += rho (J_i - BZ_i) (Eq. M3); per-agent ||J_ik - BZ_ik|| and
-// L_i(J_i, Z, Y_i) = g_i + Re tr(Y^H D) + rho/2 ||D||^2 with the new Y and BZ (Eq. sumtrace2).
-// One CTA per agent, one thread per real entry of a (direction, station) block (independent
-// loads); a block's 8 entries sit in 8 aligned lanes and are summed by shuffles, the per-direction
-// norms over the stations by one warp each (fixed order).
-__global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) {
+// BZ_i = sum_l b_l(f_i) Z_l for a Z set from outside the iteration (calib_set_consensus), with
+// the per-agent ||J_ik - BZ_ik|| and L_i(J_i, Z, Y_i) = g_i + Re tr(Y^H D) + rho/2 ||D||^2
+// (Eq. sumtrace2); Y is left as it is. One CTA per agent, one thread per real entry of a
+// (direction, station) block (independent loads); a block's 8 entries sit in 8 aligned lanes and
+// are summed by shuffles, the per-direction norms over the stations by one warp each (fixed order).
+__global__ void __launch_bounds__(CT) k_bz(const ConsArgs a) {
     __shared__ double red[33];
     extern __shared__ double dds[];  // [K][N] ||J - BZ||^2 per block
     const int agent = blockIdx.x;
@@ -198,8 +243,8 @@ __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) 
     double bl[MAX_M];
 #pragma unroll
     for (int l = 0; l < MAX_M; ++l) bl[l] = l < M ? a.basis[f * M + l] : 0.0;
-    // B Z, the difference J - B Z and the new Y in float64; the squares and the penalty terms of
-    // that difference (records only) in float32, summed in float64 across the CTA.
+    // B Z and the difference J - B Z in float64; the squares and the penalty terms of that
+    // difference (records only) in float32, summed in float64 across the CTA.
     float pen = 0.f;
     const int KN8r = (KN8 + blockDim.x - 1) / blockDim.x * blockDim.x;  // every lane runs every trip
     for (int i = threadIdx.x; i < KN8r; i += blockDim.x) {
@@ -207,7 +252,6 @@ __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) 
         float dd = 0.f;
         if (on) {
             const int k = i / (N * 8), pe = i - k * N * 8;  // pe = station * 8 + entry
-            const double rk = a.rho[k];
             const size_t o = (size_t)agent * KN8 + i;
             const double* z = a.Z + ((size_t)pb * a.K + k) * M * N * 8 + pe;  // Z[pb][k][l][p][e] at l = 0
             double bz = 0.0;
@@ -215,8 +259,7 @@ __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) 
             for (int l = 0; l < MAX_M; ++l)
                 if (l < M) bz = fma(bl[l], z[(size_t)l * N * 8], bz);
             const double d = (double)a.J[o] - bz;
-            const float ynew = update_y ? (float)((double)a.Y[o] + rk * d) : a.Y[o];
-            a.Y[o] = ynew;
+            const float ynew = a.Y[o];
             a.BZ[o] = (float)bz;
             const float df = (float)d, rf = a.rho[k];
             dd = df * df;
@@ -236,35 +279,84 @@ __global__ void __launch_bounds__(CT) k_yupdate(const ConsArgs a, int update_y) 
     if (threadIdx.x == 0) a.st[agent].L = a.st[agent].g + pen_d;
 }
 
-// Per-iteration record (Section 4): primal, dual, objective, data residual norm.
-__global__ void __launch_bounds__(CT) k_stats(const ConsArgs a) {
+// Per-iteration record (Section 4): primal, dual, objective, data residual norm, and each agent's
+// L_i = g_i + Re tr(Y^H D) + rho/2 ||D||^2 (Eq. sumtrace2) from the shares k_zy_update wrote. One
+// warp per agent, REC_AGENTS agents per CTA, every sum in a fixed order; each CTA writes its sums
+// to its own slot, and the CTA that finishes last (counted with an atomic after a fence; no CTA
+// waits) adds the slots in CTA order, writes the record and resets the count.
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(REC_AGENTS * 32) k_records(const ConsArgs a) {
+    __shared__ double sp[REC_AGENTS][3];
     __shared__ double red[33];
-    double prim = 0.0, dual = 0.0, obj = 0.0, g = 0.0;
-    for (int i = threadIdx.x; i < a.A * a.K; i += blockDim.x) prim += a.prim[i];
+    __shared__ int last_s;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int agent = blockIdx.x * REC_AGENTS + w;
     const int zs = (a.N * 8 + ZJ - 1) / ZJ;  // Z-update CTAs per (consensus problem, direction)
+    double prim = 0.0, obj = 0.0, g = 0.0;
+    if (agent < a.A) {
+        double pen = 0.0;
+        for (int k = 0; k < a.K; ++k) {
+            const size_t base = ((size_t)agent * a.K + k) * Z_SLOTS;
+            double s = 0.0, q = 0.0;
+            for (int y = lane; y < zs; y += 32) {
+                s += (double)a.prim_part[base + y];
+                q += (double)a.pen_part[base + y];
+            }
+            prim += sqrt(warp_sum_d(s));  // ||J_ik - B_i Z_k||
+            pen += warp_sum_d(q);
+        }
+        g = a.st[agent].g;
+        obj = g + pen;
+        if (lane == 0) a.st[agent].L = obj;
+    }
+    if (lane == 0) {
+        sp[w][0] = prim;
+        sp[w][1] = obj;
+        sp[w][2] = g;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < REC_AGENTS; ++i)
+            for (int c = 0; c < 3; ++c) t[c] += sp[i][c];
+        for (int c = 0; c < 3; ++c) a.rec_part[(size_t)blockIdx.x * 3 + c] = t[c];
+        __threadfence();
+        last_s = atomicAdd(a.rec_count, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last_s) return;
+    __threadfence();
+    double pr = 0.0, dual = 0.0, ob = 0.0, gg = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        pr += __ldcg(a.rec_part + (size_t)i * 3 + 0);
+        ob += __ldcg(a.rec_part + (size_t)i * 3 + 1);
+        gg += __ldcg(a.rec_part + (size_t)i * 3 + 2);
+    }
     for (int i = threadIdx.x; i < a.I * a.G * a.K; i += blockDim.x) {
         double d2 = 0.0;
         for (int y = 0; y < zs; ++y) d2 += a.dual2[(size_t)i * Z_SLOTS + y];
         dual += sqrt(d2);
     }
-    for (int i = threadIdx.x; i < a.A; i += blockDim.x) {
-        obj += a.st[i].L;
-        g += a.st[i].g;
-    }
-    prim = bsum(prim, red);
+    pr = bsum(pr, red);
     dual = bsum(dual, red);
-    obj = bsum(obj, red);
-    g = bsum(g, red);
+    ob = bsum(ob, red);
+    gg = bsum(gg, red);
     if (threadIdx.x == 0) {
         const int it = *a.iter_counter;
         if (it < a.max_iters) {
             double* o = a.stats + (size_t)it * 4;
-            o[0] = prim / sqrt(4.0 * a.N) / ((double)a.A * a.K);
+            o[0] = pr / sqrt(4.0 * a.N) / ((double)a.A * a.K);
             o[1] = dual / sqrt(4.0 * a.M * a.N) / ((double)a.I * a.G * a.K);
-            o[2] = obj;
-            o[3] = sqrt(g);
+            o[2] = ob;
+            o[3] = sqrt(gg);
         }
         *a.iter_counter = it + 1;
+        *a.rec_count = 0;
     }
 }
 
@@ -282,22 +374,18 @@ cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s) {
     k_gauge<<<a.A, CT, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_zupdate(const ConsArgs& a, cudaStream_t s) {
+cudaError_t launch_zy_update(const ConsArgs& a, cudaStream_t s) {
     const int zs = (a.N * 8 + ZJ - 1) / ZJ;
     if (zs > Z_SLOTS || a.M > MAX_M) return cudaErrorInvalidConfiguration;
-    k_zupdate<<<dim3(a.I * a.G * a.K, zs), ZJ * ZG, 0, s>>>(a);
-    return cudaGetLastError();
-}
-cudaError_t launch_yupdate(const ConsArgs& a, cudaStream_t s) {
-    k_yupdate<<<a.A, CT, (size_t)a.K * a.N * sizeof(double), s>>>(a, 1);
+    k_zy_update<<<dim3(a.I * a.G * a.K, zs), ZJ * ZG, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_bz_only(const ConsArgs& a, cudaStream_t s) {
-    k_yupdate<<<a.A, CT, (size_t)a.K * a.N * sizeof(double), s>>>(a, 0);
+    k_bz<<<a.A, CT, (size_t)a.K * a.N * sizeof(double), s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_stats(const ConsArgs& a, cudaStream_t s) {
-    k_stats<<<1, CT, 0, s>>>(a);
+cudaError_t launch_records(const ConsArgs& a, cudaStream_t s) {
+    k_records<<<(a.A + REC_AGENTS - 1) / REC_AGENTS, REC_AGENTS * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_identity(float* J, long long n_blocks, cudaStream_t s) {

@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include "calib_internal.cuh"
+#include "df.cuh"
 
 namespace calib {
 namespace {
@@ -162,26 +163,6 @@ __device__ __forceinline__ float penalty_decrease_blk(const Blk& j, const Blk& j
 // built from error-free float32 transformations (the exact product error by FMA, Dekker 1971;
 // the exact sum error by TwoSum, Knuth TAOCP vol. 2, 4.2.2). The 4x4 system is well conditioned
 // (S is the Gram matrix of J_k) and is solved in float32 in closed form.
-struct DF { float hi, lo; };
-
-__device__ __forceinline__ void df_add_prod(DF& s, float a, float b) {
-    const float p = __fmul_rn(a, b);
-    const float e = __fmaf_rn(a, b, -p);  // a*b - p, exact
-    const float t = __fadd_rn(s.hi, p);
-    const float z = __fsub_rn(t, s.hi);
-    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, z)), __fsub_rn(p, z));  // s.hi + p - t, exact
-    s.hi = t;
-    s.lo = __fadd_rn(s.lo, __fadd_rn(err, e));
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    const float t = __fadd_rn(a.hi, b.hi);
-    const float z = __fsub_rn(t, a.hi);
-    const float err = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(t, z)), __fsub_rn(b.hi, z));
-    const float lo = __fadd_rn(__fadd_rn(a.lo, b.lo), err);
-    const float hi = __fadd_rn(t, lo);
-    return DF{hi, __fsub_rn(lo, __fsub_rn(hi, t))};
-}
-
 constexpr int GT = 12;  // per-block gauge terms: 4 double-float (t0, t1, 2 t2, 2 t3) and s0, s1, u, w
 
 // This block's terms of skew(J^H G) and J^H J. Row m, column c of a block: v[m*4 + c*2 + (0 re, 1 im)].
