@@ -46,8 +46,8 @@ UNIT = "vis*dir*iter/s"
 # DRAM traffic per launch of each sweep kernel from one ncu capture; valid only for the kernel
 # source it was taken on (sha256 prefix of the kernel's .cu file), else reported as null.
 NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum of one full capture each (summaries in profiles/)
-    ("stats_hessvec", "fa12258caf66"): 81.27e6,
-    ("stats_trial", "c93f6cd6f93a"): 181.2e6,
+    ("stats_hessvec", "effefc092027"): 82.56e6,
+    ("stats_trial", "7102e7ad44aa"): 181.1e6,
     ("stats_pass", "532c6d147726"): 595.5e6,
     ("residual", "532c6d147726"): 615.2e6,
 }

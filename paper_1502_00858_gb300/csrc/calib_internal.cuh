@@ -137,7 +137,7 @@ struct LMArgs {
 // Z-update CTAs per (consensus problem, direction) at most: 32 (station, entry) positions each, N <= 128.
 constexpr int Z_SLOTS = 32;
 // Agents per CTA of the per-iteration record kernel (one warp each).
-constexpr int REC_AGENTS = 8;
+constexpr int REC_AGENTS = 2;
 
 struct ConsArgs {
     float* J; float* gradg; float* Gm; float* Y; float* BZ;

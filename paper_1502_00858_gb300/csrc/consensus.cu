@@ -130,9 +130,11 @@ __global__ void __launch_bounds__(CT) k_gauge(const ConsArgs a) {
 constexpr int ZJ = 32;  // (station, entry) positions per CTA: one per lane
 constexpr int ZG = 4;   // warps per CTA, each over every ZG-th agent of the problem
 
+// MB: the basis size rounded up to a compiled bucket (every loop over the basis is unrolled to MB).
+template <int MB>
 __global__ void __launch_bounds__(ZJ * ZG) k_zy_update(const ConsArgs a) {
-    __shared__ float2 Rs[ZG - 1][MAX_M][ZJ];
-    __shared__ float2 Zs[MAX_M][ZJ];
+    __shared__ float2 Rs[ZG - 1][MB][ZJ];
+    __shared__ float2 Zs[MB][ZJ];
     __shared__ double red[33];
     const int ivk = blockIdx.x;  // (consensus problem, direction)
     const int k = ivk % a.K, pb = ivk / a.K;
@@ -144,9 +146,9 @@ __global__ void __launch_bounds__(ZJ * ZG) k_zy_update(const ConsArgs a) {
     const float rk = a.rho[k];
     const size_t stride = (size_t)a.G * a.K * NE;  // next agent of the problem, same direction
     const size_t o0 = (((size_t)iv * a.P + g) * a.K + k) * NE + j;
-    DF R[MAX_M];
+    DF R[MB];
 #pragma unroll
-    for (int l = 0; l < MAX_M; ++l) R[l] = DF{0.f, 0.f};
+    for (int l = 0; l < MB; ++l) R[l] = DF{0.f, 0.f};
     if (on) {
 #pragma unroll 2
         for (int jj = grp; jj < Pg; jj += ZG) {
@@ -154,13 +156,13 @@ __global__ void __launch_bounds__(ZJ * ZG) k_zy_update(const ConsArgs a) {
             const DF v = df_add(df_prod(rk, __ldg(a.J + o)), DF{__ldg(a.Y + o), 0.f});  // Y + rho J
             const float2* bf = a.basis_df + (size_t)(g + a.G * jj) * M;
 #pragma unroll
-            for (int l = 0; l < MAX_M; ++l)
+            for (int l = 0; l < MB; ++l)
                 if (l < M) R[l] = df_fma(df_load(bf + l), v, R[l]);
         }
     }
     if (grp > 0) {
 #pragma unroll
-        for (int l = 0; l < MAX_M; ++l)
+        for (int l = 0; l < MB; ++l)
             if (l < M) Rs[grp - 1][l][lane] = make_float2(R[l].hi, R[l].lo);
     }
     __syncthreads();
@@ -169,16 +171,16 @@ __global__ void __launch_bounds__(ZJ * ZG) k_zy_update(const ConsArgs a) {
 #pragma unroll
         for (int w = 0; w < ZG - 1; ++w)
 #pragma unroll
-            for (int l = 0; l < MAX_M; ++l)
+            for (int l = 0; l < MB; ++l)
                 if (l < M) R[l] = df_add(R[l], df_load(&Rs[w][l][lane]));
         const float2* Pinv = a.Pinv_df + (size_t)g * M * M;
         const DF ri = df_load(a.rinv_df + k);
 #pragma unroll
-        for (int l = 0; l < MAX_M; ++l) {
+        for (int l = 0; l < MB; ++l) {
             if (l >= M) continue;
             DF z{0.f, 0.f};
 #pragma unroll
-            for (int m = 0; m < MAX_M; ++m)
+            for (int m = 0; m < MB; ++m)
                 if (m < M) z = df_fma(df_load(Pinv + l * M + m), R[m], z);
             z = df_mul(z, ri);
             const size_t zo = (((size_t)pb * a.K + k) * M + l) * NE + j;
@@ -192,9 +194,9 @@ __global__ void __launch_bounds__(ZJ * ZG) k_zy_update(const ConsArgs a) {
     dz2 = bsum(dz2, red);  // its barriers also publish Zs
     if (threadIdx.x == 0) a.dual2[(size_t)ivk * Z_SLOTS + blockIdx.y] = dz2;
 
-    DF zl[MAX_M];
+    DF zl[MB];
 #pragma unroll
-    for (int l = 0; l < MAX_M; ++l) zl[l] = (on && l < M) ? df_load(&Zs[l][lane]) : DF{0.f, 0.f};
+    for (int l = 0; l < MB; ++l) zl[l] = (on && l < M) ? df_load(&Zs[l][lane]) : DF{0.f, 0.f};
     for (int jj = grp; jj < Pg; jj += ZG) {  // the same trip count in every lane of the warp
         const int f = g + a.G * jj;
         float dd = 0.f, pen = 0.f;
@@ -203,7 +205,7 @@ __global__ void __launch_bounds__(ZJ * ZG) k_zy_update(const ConsArgs a) {
             const float2* bf = a.basis_df + (size_t)f * M;
             DF bz{0.f, 0.f};
 #pragma unroll
-            for (int l = 0; l < MAX_M; ++l)
+            for (int l = 0; l < MB; ++l)
                 if (l < M) bz = df_fma(df_load(bf + l), zl[l], bz);
             const float y = a.Y[o];
             const DF d = df_add(DF{a.J[o], 0.f}, df_neg(bz));  // J - B Z
@@ -284,7 +286,7 @@ __global__ void __launch_bounds__(CT) k_bz(const ConsArgs a) {
 // warp per agent, REC_AGENTS agents per CTA, every sum in a fixed order; each CTA writes its sums
 // to its own slot, and the CTA that finishes last (counted with an atomic after a fence; no CTA
 // waits) adds the slots in CTA order, writes the record and resets the count.
-__device__ __forceinline__ double warp_sum_d(double v) {
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
@@ -299,19 +301,20 @@ __global__ void __launch_bounds__(REC_AGENTS * 32) k_records(const ConsArgs a) {
     const int zs = (a.N * 8 + ZJ - 1) / ZJ;  // Z-update CTAs per (consensus problem, direction)
     double prim = 0.0, obj = 0.0, g = 0.0;
     if (agent < a.A) {
-        double pen = 0.0;
+        // the float32 shares are summed in float32 (the records' precision); the agents in float64
+        float pen = 0.f;
         for (int k = 0; k < a.K; ++k) {
             const size_t base = ((size_t)agent * a.K + k) * Z_SLOTS;
-            double s = 0.0, q = 0.0;
+            float s = 0.f, q = 0.f;
             for (int y = lane; y < zs; y += 32) {
-                s += (double)a.prim_part[base + y];
-                q += (double)a.pen_part[base + y];
+                s += a.prim_part[base + y];
+                q += a.pen_part[base + y];
             }
-            prim += sqrt(warp_sum_d(s));  // ||J_ik - B_i Z_k||
-            pen += warp_sum_d(q);
+            prim += (double)sqrtf(warp_sum_f(s));  // ||J_ik - B_i Z_k||
+            pen += warp_sum_f(q);
         }
         g = a.st[agent].g;
-        obj = g + pen;
+        obj = g + (double)pen;
         if (lane == 0) a.st[agent].L = obj;
     }
     if (lane == 0) {
@@ -377,7 +380,15 @@ cudaError_t launch_gauge(const ConsArgs& a, cudaStream_t s) {
 cudaError_t launch_zy_update(const ConsArgs& a, cudaStream_t s) {
     const int zs = (a.N * 8 + ZJ - 1) / ZJ;
     if (zs > Z_SLOTS || a.M > MAX_M) return cudaErrorInvalidConfiguration;
-    k_zy_update<<<dim3(a.I * a.G * a.K, zs), ZJ * ZG, 0, s>>>(a);
+    const dim3 grid(a.I * a.G * a.K, zs);
+    if (a.M <= 2)
+        k_zy_update<2><<<grid, ZJ * ZG, 0, s>>>(a);
+    else if (a.M <= 4)
+        k_zy_update<4><<<grid, ZJ * ZG, 0, s>>>(a);
+    else if (a.M <= 8)
+        k_zy_update<8><<<grid, ZJ * ZG, 0, s>>>(a);
+    else
+        k_zy_update<MAX_M><<<grid, ZJ * ZG, 0, s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_bz_only(const ConsArgs& a, cudaStream_t s) {
