@@ -133,7 +133,7 @@ constexpr int ZG = 4;   // warps per CTA, each over every ZG-th agent of the pro
 // MB: the basis size rounded up to a compiled bucket (every loop over the basis is unrolled to MB).
 template <int MB>
 __global__ void __launch_bounds__(ZJ * ZG) k_zy_update(const ConsArgs a) {
-    __shared__ float2 Rs[ZG - 1][MB][ZJ];
+    __shared__ float2 Rs[ZG][MB][ZJ];
     __shared__ float2 Zs[MB][ZJ];
     __shared__ double red[33];
     const int ivk = blockIdx.x;  // (consensus problem, direction)
@@ -160,24 +160,24 @@ __global__ void __launch_bounds__(ZJ * ZG) k_zy_update(const ConsArgs a) {
                 if (l < M) R[l] = df_fma(df_load(bf + l), v, R[l]);
         }
     }
-    if (grp > 0) {
 #pragma unroll
-        for (int l = 0; l < MB; ++l)
-            if (l < M) Rs[grp - 1][l][lane] = make_float2(R[l].hi, R[l].lo);
-    }
+    for (int l = 0; l < MB; ++l)
+        if (l < M) Rs[grp][l][lane] = make_float2(R[l].hi, R[l].lo);
     __syncthreads();
+    // the warps' sums added in warp order (R_m identical in every warp); warp w forms the Z_l with
+    // l = w mod ZG
     double dz2 = 0.0;
-    if (grp == 0 && on) {
+    if (on) {
 #pragma unroll
-        for (int w = 0; w < ZG - 1; ++w)
+        for (int m = 0; m < MB; ++m) {
+            if (m >= M) continue;
+            R[m] = df_load(&Rs[0][m][lane]);
 #pragma unroll
-            for (int l = 0; l < MB; ++l)
-                if (l < M) R[l] = df_add(R[l], df_load(&Rs[w][l][lane]));
+            for (int w = 1; w < ZG; ++w) R[m] = df_add(R[m], df_load(&Rs[w][m][lane]));
+        }
         const float2* Pinv = a.Pinv_df + (size_t)g * M * M;
         const DF ri = df_load(a.rinv_df + k);
-#pragma unroll
-        for (int l = 0; l < MB; ++l) {
-            if (l >= M) continue;
+        for (int l = grp; l < M; l += ZG) {
             DF z{0.f, 0.f};
 #pragma unroll
             for (int m = 0; m < MB; ++m)
@@ -302,18 +302,25 @@ __global__ void __launch_bounds__(REC_AGENTS * 32) k_records(const ConsArgs a) {
     double prim = 0.0, obj = 0.0, g = 0.0;
     if (agent < a.A) {
         // the float32 shares are summed in float32 (the records' precision); the agents in float64
-        float pen = 0.f;
-        for (int k = 0; k < a.K; ++k) {
-            const size_t base = ((size_t)agent * a.K + k) * Z_SLOTS;
-            float s = 0.f, q = 0.f;
-            for (int y = lane; y < zs; y += 32) {
-                s += a.prim_part[base + y];
-                q += a.pen_part[base + y];
+        // lane y holds chunk y (zs <= 32) of every direction: all loads are issued together
+        float s[MAX_K], q[MAX_K];
+#pragma unroll
+        for (int k = 0; k < MAX_K; ++k) {
+            s[k] = q[k] = 0.f;
+            if (k < a.K && lane < zs) {
+                const size_t i = ((size_t)agent * a.K + k) * Z_SLOTS + lane;
+                s[k] = a.prim_part[i];
+                q[k] = a.pen_part[i];
             }
-            prim += (double)sqrtf(warp_sum_f(s));  // ||J_ik - B_i Z_k||
-            pen += warp_sum_f(q);
         }
         g = a.st[agent].g;
+        float pen = 0.f;
+#pragma unroll
+        for (int k = 0; k < MAX_K; ++k) {
+            if (k >= a.K) continue;
+            prim += (double)sqrtf(warp_sum_f(s[k]));  // ||J_ik - B_i Z_k||
+            pen += warp_sum_f(q[k]);
+        }
         obj = g + (double)pen;
         if (lane == 0) a.st[agent].L = obj;
     }
