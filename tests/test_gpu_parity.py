@@ -284,6 +284,15 @@ HISTORY_CASES = ["tiny_n8_k1", "ragged_n13_k3", "n2_single_baseline", "n10_k10_f
 @pytest.mark.parametrize("case,form", [(c, f) for c in HISTORY_CASES for f in sorted(FORMS)
                                        if not (c in DIRECT_ONLY and f == "statistics")])
 def test_admm_history_matches_oracle(lib, case, form):
+    """Whole C-ADMM histories. The dual residual (differences of consecutive Z) is held at 1e-3
+    where the basis amplifies J into Z by less than 10 (measured: 2e-4 at most, on the ragged
+    case; 7e-6 or less on the others), with an absolute floor of 1e-5 of its first record where it
+    has fallen to round-off. The tiny case's ordinary-polynomial basis amplifies by 20.7: there the
+    float32 round-off in the weakly curved gauge mode of its direction moves Z once the iteration
+    has settled, and the dual, which measures exactly that motion, differs by up to 24 % (band
+    0.015 x amplification). The dual's definition and normalisation (Section 4) are held at 1e-4 by
+    test_admm_one_lm_step_matches_all_records, where the gauge mode is not yet resolved, and pinned
+    by hand in tests/test_oracle_schedule_pins.py."""
     prob = CASES[case]()
     n_iter = 10 if case == "tiny_n8_k1" else 4
     _, hist, ref = run_both(lib, prob, n_iter, form=form)
@@ -292,7 +301,8 @@ def test_admm_history_matches_oracle(lib, case, form):
     np.testing.assert_allclose(hist["primal"], ref["primal"], rtol=1e-3, atol=1e-7)
     basis = prob["basis"]
     amp = np.linalg.norm(np.linalg.pinv(basis.T @ basis) @ basis.T, 2)
-    np.testing.assert_allclose(hist["dual"], ref["dual"], rtol=max(0.15, 0.015 * amp), atol=1e-5 * ref["dual"][0])
+    band = 1e-3 if amp < 10 else max(0.15, 0.015 * amp)
+    np.testing.assert_allclose(hist["dual"], ref["dual"], rtol=band, atol=1e-5 * ref["dual"][0])
 
 
 @pytest.mark.parametrize("form", sorted(FORMS))

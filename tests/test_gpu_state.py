@@ -103,3 +103,20 @@ def test_blobs_of_another_problem_or_damaged_blobs_are_rejected(lib):
     unflagged.close()
     other.close()
     cal.close()
+
+
+@pytest.mark.parametrize("form", sorted(FORMS))
+def test_dependent_launch_changes_no_result(lib, form):
+    """In the timed graph the LM chain's kernels run under programmatic dependent launch: each may
+    start while the one before it is still running and waits (griddepcontrol.wait) before it touches
+    that kernel's outputs. With per-kernel profiling on, the graph has event records between the
+    kernels and runs them strictly one after another. Both give the same records and solutions bit
+    for bit."""
+    prob = ragged()
+    out = []
+    for profiling in (False, True):
+        cal = calibrator(prob, form)
+        capi.calib_profile_enable(cal.ctx, profiling)
+        out.append(run(cal, 4))
+        cal.close()
+    assert_same(out[0], out[1])
