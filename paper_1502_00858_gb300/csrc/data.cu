@@ -77,6 +77,7 @@ __global__ void k_extract_coh(const IngestArgs a, float2* out) {
 // direction k0, R <- J_i,k0^-1 R J_j,k0^-H. A pair held reversed is written back as R^H, which is
 // the user-order residual (and correction) of the same baseline. One CTA per (diagonal, agent), one
 // thread per slot looping over the samples; reads V and C once and writes each residual once.
+// Each M_k = J_ik J_jk^H is formed once per slot (below), not once per sample.
 struct cf { float x, y; };
 __device__ __forceinline__ cf cmulf(cf a, cf b) { return cf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
 __device__ __forceinline__ cf cmulcf(cf a, cf b) { return cf{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }  // conj(a) b
@@ -117,15 +118,21 @@ __device__ __forceinline__ m22 mherm(const m22& A) {
     return o;
 }
 
-__global__ void __launch_bounds__(64) k_residual(const ResidualArgs a) {
-    const int d = blockIdx.x, agent = blockIdx.y;
+constexpr int RES_THREADS = 64;
+
+// Before its sample loop a thread forms its slot's model matrices M_k = J_ik J_jk^H of the masked
+// directions into its own column of shared memory (Ms: [K][2 rows][RES_THREADS] float4; no thread
+// reads another's), so the loop over the samples reads only V, C and M.
+__global__ void __launch_bounds__(RES_THREADS) k_residual(const ResidualArgs a) {
+    extern __shared__ float4 Ms[];
+    const int d = blockIdx.x, agent = blockIdx.y, tid = threadIdx.x;
     const DiagDesc dsc = a.desc[(size_t)agent * a.D + d];
     const int Ta = a.T[agent], K = a.K, N = a.N;
-    const float4* J = reinterpret_cast<const float4*>(a.J) + (size_t)agent * K * N * 2;  // [K][N][2 rows]
-    const float4* V = reinterpret_cast<const float4*>(a.V + dsc.voff);                 // [T][n_pad][2 rows]
-    const float2* C = a.C + dsc.coff;                                                   // [T][n_pad][K]
-    float4* out = reinterpret_cast<float4*>(a.out + a.vis_off[agent]);                 // [B][T_a][2 rows]
-    for (int g = threadIdx.x; g < dsc.n; g += blockDim.x) {
+    const float4* __restrict__ J = reinterpret_cast<const float4*>(a.J) + (size_t)agent * K * N * 2;  // [K][N][2 rows]
+    const float4* __restrict__ V = reinterpret_cast<const float4*>(a.V + dsc.voff);                 // [T][n_pad][2 rows]
+    const float2* __restrict__ C = a.C + dsc.coff;                                                   // [T][n_pad][K]
+    float4* __restrict__ out = reinterpret_cast<float4*>(a.out + a.vis_off[agent]);                 // [B][T_a][2 rows]
+    for (int g = tid; g < dsc.n; g += RES_THREADS) {
         const int sl = a.slot[dsc.slot_off + g];
         const int i = sl & 0xff, j = (sl >> 8) & 0xff, rev = (sl >> 16) & 1;
         const long long b = a.slot_b[dsc.slot_off + g];
@@ -134,6 +141,18 @@ __global__ void __launch_bounds__(64) k_residual(const ResidualArgs a) {
             Li = minv(ld_m22(J + ((size_t)a.correct * N + i) * 2));
             Rj = mherm(minv(ld_m22(J + ((size_t)a.correct * N + j) * 2)));
         }
+        for (int k = 0; k < K; ++k) {
+            if (!((a.mask >> k) & 1u)) continue;
+            const m22 Ji = ld_m22(J + ((size_t)k * N + i) * 2), Jj = ld_m22(J + ((size_t)k * N + j) * 2);
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                // (J_i J_j^H)[r][cc] = J_i[r][0] conj(J_j[cc][0]) + J_i[r][1] conj(J_j[cc][1])
+                const cf m0 = caddf(cmulcf(Jj.e[0][0], Ji.e[r][0]), cmulcf(Jj.e[0][1], Ji.e[r][1]));
+                const cf m1 = caddf(cmulcf(Jj.e[1][0], Ji.e[r][0]), cmulcf(Jj.e[1][1], Ji.e[r][1]));
+                Ms[(k * 2 + r) * RES_THREADS + tid] = make_float4(m0.x, m0.y, m1.x, m1.y);
+            }
+        }
+#pragma unroll 2
         for (int t = 0; t < Ta; ++t) {
             const size_t pos = (size_t)t * dsc.n_pad + g;
             m22 R = ld_m22(V + pos * 2);
@@ -141,16 +160,16 @@ __global__ void __launch_bounds__(64) k_residual(const ResidualArgs a) {
                 if (!((a.mask >> k) & 1u)) continue;
                 const float2 c2 = __ldg(C + pos * K + k);
                 const cf c{c2.x, c2.y};
-                const m22 Ji = ld_m22(J + ((size_t)k * N + i) * 2), Jj = ld_m22(J + ((size_t)k * N + j) * 2);
 #pragma unroll
-                for (int r = 0; r < 2; ++r)
+                for (int r = 0; r < 2; ++r) {
+                    const float4 q = Ms[(k * 2 + r) * RES_THREADS + tid];
+                    const cf m[2] = {cf{q.x, q.y}, cf{q.z, q.w}};
 #pragma unroll
                     for (int cc = 0; cc < 2; ++cc) {
-                        // (J_i J_j^H)[r][cc] = J_i[r][0] conj(J_j[cc][0]) + J_i[r][1] conj(J_j[cc][1])
-                        const cf m = caddf(cmulcf(Jj.e[cc][0], Ji.e[r][0]), cmulcf(Jj.e[cc][1], Ji.e[r][1]));
-                        const cf cm = cmulf(c, m);
+                        const cf cm = cmulf(c, m[cc]);
                         R.e[r][cc] = cf{R.e[r][cc].x - cm.x, R.e[r][cc].y - cm.y};
                     }
+                }
             }
             if (a.correct >= 0) R = mmul(mmul(Li, R), Rj);
             if (rev) R = mherm(R);
@@ -393,7 +412,7 @@ cudaError_t launch_extract_coh(const IngestArgs& a, float2* user_dst, cudaStream
 }
 cudaError_t launch_residual(const ResidualArgs& a, cudaStream_t s) {
     dim3 grid(a.D, a.A);
-    k_residual<<<grid, 64, 0, s>>>(a);
+    k_residual<<<grid, RES_THREADS, (size_t)a.K * 2 * RES_THREADS * sizeof(float4), s>>>(a);
     return cudaGetLastError();
 }
 cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s) {

@@ -140,12 +140,18 @@ def training_pairs(prob, n_transitions, n_iter=30):
     return X0, T
 
 
+# Relative tolerances of the steps-to-target table: g <= (1 + eps) x the cold start's n_iter-iteration cost.
+TOLERANCES = (0.0, 1e-5, 3e-5, 1e-4, 3e-4, 1e-3)
+
+
 def time_to_residual(prob, net, n_eval, n_iter=30, eval_n_lm=10):
     """For intervals 1..n_eval of a drifting sequence: the plain cold start's residual after n_iter
     iterations (10 LM steps each) is the target; report the iterations and wall time the
     previous-solution start and the network start need to reach it (per interval), plus the
     fraction of agents where the network's start was kept. eval_n_lm sets the LM steps per C-ADMM
-    iteration of the two warm starts (1 counts single LM steps: a finer measure of the start)."""
+    iteration of the two warm starts (1 counts single LM steps: a finer measure of the start).
+    Also, per warm start, the iterations each interval needs to come within a relative tolerance of
+    the target (TOLERANCES) and the mean excess data cost after each of the first iterations."""
     import torch
 
     P = prob["P"]
@@ -179,12 +185,20 @@ def time_to_residual(prob, net, n_eval, n_iter=30, eval_n_lm=10):
         L0, g0, _ = cal.eval(J0)  # objective and data cost at the start
         need = np.full(len(cur), -1)
         g_first = None
+        ratio = []  # per iteration: each interval's data cost / target
         for it in range(1, n_iter + 1):
             cal.iterate(1, want_hist=False)
             g = interval_g(cal, P)
+            ratio.append(g / target)
             if it == 1:
                 g_first = g.copy()
             need[(need < 0) & (g <= target)] = it
+        ratio = np.array(ratio)
+        within = {}
+        for eps in TOLERANCES:  # iterations until g <= (1 + eps) target, per interval
+            hit = ratio <= 1.0 + eps
+            steps = np.where(hit.any(0), hit.argmax(0) + 1, n_iter + 1)
+            within[f"{eps:g}"] = dict(median=float(np.median(steps)), mean=float(steps.mean()), max=int(steps.max()))
         reached = need[need > 0]
         n_max = int(reached.max()) if reached.size else n_iter
         # wall time of a batched run of that many iterations from the same start
@@ -199,7 +213,9 @@ def time_to_residual(prob, net, n_eval, n_iter=30, eval_n_lm=10):
                          iters_max=n_max, reached=int(reached.size), of=len(cur), seconds=secs,
                          network_kept=float(chose.mean()) if use_net else 0.0,
                          start_objective=float(L0.sum()), start_data_cost_over_target=float(g0.sum() / target.sum()),
-                         after_one_iter_data_cost_over_target=float(g_first.sum() / target.sum()))
+                         after_one_iter_data_cost_over_target=float(g_first.sum() / target.sum()),
+                         iters_to_within=within,
+                         mean_excess_after=[float(ratio[i].mean() - 1.0) for i in range(min(5, n_iter))])
     cal.close()
     return out
 

@@ -122,4 +122,7 @@ def test_warm_starts_reach_the_cold_residual_sooner(small_sequence):
     # higher; on this sequence it also starts closer to the target data cost
     assert res["network"]["start_objective"] <= res["previous"]["start_objective"] * (1 + 1e-9)
     assert res["network"]["start_data_cost_over_target"] < res["previous"]["start_data_cost_over_target"]
+    # counted in single LM steps, the network's start stays closer after the first step too
+    res1 = W.time_to_residual(prob, net, n_eval=4, n_iter=10, eval_n_lm=1)
+    assert res1["network"]["mean_excess_after"][0] < res1["previous"]["mean_excess_after"][0]
     net.close()
