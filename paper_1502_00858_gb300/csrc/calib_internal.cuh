@@ -146,7 +146,7 @@ struct ConsArgs {
     const double* Pinv;     // [M][M] (sum_i b_i b_i^T)^-1
     const float* rho;       // [K]
     AgentState* st;
-    double* prim;           // [A][K] ||J_ik - B_i Z_k||
+    double* prim;           // [A][K] ||J_ik - B_i Z_k|| after k_bz (the iteration's records use prim_part)
     double* dual2;          // [I * G][K][Z_SLOTS] per-CTA shares of ||Z_k^{n+1} - Z_k^n||^2
     const float2* basis_df; // [P][M] the basis as double-float (hi, lo) pairs
     const float2* Pinv_df;  // [G][M][M] Pinv as double-float pairs
