@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(RES_THREADS) k_residual(const ResidualArgs a) 
 
 // One CTA per (sample, agent); source chunks sized to fit the phasor table in shared memory.
 __global__ void __launch_bounds__(256) k_predict(const PredictArgs a, int s_chunk) {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];  // one declaration for the file's kernels
     const int t = blockIdx.x, agent = blockIdx.y;
     const int Ta = a.T[agent];
     if (t >= Ta) return;
