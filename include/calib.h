@@ -8,10 +8,15 @@
  * separately, Section 4) are batched the same way. One call of calib_admm_iter runs
  * C-ADMM iterations (Section 3, Eq. M1-M3, steps D1-D3):
  *
- *   M1  J_i <- argmin_J L_i(J, Z, Y_i)       per agent, by Levenberg-Marquardt with a
- *                                            preconditioned CG step (the paper uses RTR)
+ *   M1  J_i <- argmin_J L_i(J, Z, Y_i)       per agent, by Levenberg-Marquardt with
+ *                                            preconditioned CG steps (default), or by the
+ *                                            paper's RTR or SAGE (calib_options.jupdate)
  *   M2  Z   <- closed form of Eq. Zest        per interval and direction (fusion centre)
  *   M3  Y_i <- Y_i + rho (J_i - B_i Z)        per agent
+ *
+ * J and Y are float32; Z is stored in float64 and M2/M3 are computed in double-float
+ * arithmetic (pairs of float32, about 48 bits). Every reduction runs in a fixed order, so a
+ * call repeats bit for bit (calib_eval_noalloc, whose sums use atomics, excepted).
  *
  * with L_i(J,Z,Y) = g(J) + Re tr(Y^H (J - B Z)) + rho/2 ||J - B Z||^2 (Eq. sumtrace2),
  * g(J) = sum_t sum_{p<q} ||V_pq - sum_k J_pk C_pqk J_qk^H||^2 (Eq. mltheta / Eq. sum3)
