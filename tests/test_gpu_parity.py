@@ -305,6 +305,26 @@ def test_admm_history_matches_oracle(lib, case, form):
     np.testing.assert_allclose(hist["dual"], ref["dual"], rtol=band, atol=1e-5 * ref["dual"][0])
 
 
+@pytest.mark.parametrize("degree", [5, 9])
+def test_admm_history_with_a_larger_basis(lib, degree):
+    """Basis sizes M = 6 and 10 over 12 frequencies run the fusion-centre kernel's 8- and 16-term
+    buckets; the records follow the oracle as in the history test. The basis is the orthonormalised
+    span of the Bernstein polynomials of degree 5 and 9 (QR): the same fit space, well conditioned
+    (amplification 1 from J to Z), so the dual is held at 1e-3."""
+    from synth.lofar import basis_matrix
+
+    prob = make_problem("tiny_n8_k1", P=12, seed=24)
+    basis = np.linalg.qr(basis_matrix("bernstein", degree, prob["freqs"]))[0]
+    prob = dict(prob, basis=basis, M=basis.shape[1])
+    _, hist, ref = run_both(lib, prob, 4)
+    np.testing.assert_allclose(hist["objective"], ref["objective"], rtol=REL_ADMM)
+    np.testing.assert_allclose(hist["resid_norm"], ref["resid_norm"], rtol=REL_ADMM)
+    np.testing.assert_allclose(hist["primal"], ref["primal"], rtol=1e-3, atol=1e-7)
+    amp = np.linalg.norm(np.linalg.pinv(basis.T @ basis) @ basis.T, 2)
+    band = 1e-3 if amp < 10 else max(0.15, 0.015 * amp)
+    np.testing.assert_allclose(hist["dual"], ref["dual"], rtol=band, atol=1e-5 * ref["dual"][0])
+
+
 @pytest.mark.parametrize("form", sorted(FORMS))
 @pytest.mark.parametrize("case,n_cg", [("n3_k2", 1), ("tiny_n8_k1", 4), ("ragged_n13_k3", 4)])
 def test_admm_one_lm_step_matches_all_records(lib, case, n_cg, form):
