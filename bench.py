@@ -48,8 +48,8 @@ UNIT = "vis*dir*iter/s"
 NCU_TRAFFIC = {  # dram__bytes_read.sum + dram__bytes_write.sum of one full capture each (summaries in profiles/)
     ("stats_hessvec", "effefc092027"): 82.56e6,
     ("stats_trial", "7102e7ad44aa"): 181.1e6,
-    ("stats_pass", "6309f7fca47e"): 595.5e6,
-    ("residual", "6309f7fca47e"): 619.0e6,
+    ("stats_pass", "fbe001eb534e"): 592.6e6,
+    ("residual", "fbe001eb534e"): 618.7e6,
 }
 KERNEL_SOURCE = {"sweep_residual": "sweep.cu", "sweep_hessvec": "sweep.cu", "stats_hessvec": "ss_hessvec.cu",
                  "stats_trial": "ss.cu", "stats_pass": "data.cu", "residual": "data.cu"}

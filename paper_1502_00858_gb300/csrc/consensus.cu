@@ -38,37 +38,52 @@ __device__ __forceinline__ C2 cadd(C2 a, C2 b) { return {a.r + b.r, a.i + b.i}; 
 // det M = |det M| e^{i theta}: U = (M + e^{i theta} adj(M)^H) / sqrt(||M||_F^2 + 2 |det M|).
 // The stored data gradient and Jacobi blocks are rotated with J (grad g(JU) = grad g(J) U,
 // G(JU) = U^H G U) since g is invariant under the common unitary.
+// One warp per direction: M accumulated over the stations in float32 and reduced across the warp,
+// U formed from it in float64 by lane 0 and broadcast, and J, the gradient and G rotated in float32
+// (they are float32 data).
+__device__ __forceinline__ float warp_sum_f32(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+struct F2 { float r, i; };
+__device__ __forceinline__ F2 fm(F2 a, F2 b) { return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r}; }
+__device__ __forceinline__ F2 fcm(F2 a, F2 b) { return {a.r * b.r + a.i * b.i, a.r * b.i - a.i * b.r}; }  // conj(a) b
+__device__ __forceinline__ F2 fadd(F2 a, F2 b) { return {a.r + b.r, a.i + b.i}; }
+
 __global__ void __launch_bounds__(CT) k_gauge(const ConsArgs a) {
-    __shared__ double red[33];
-    __shared__ C2 U[4];
     const int agent = blockIdx.x;
     const int iv = agent / a.P, f = agent - iv * a.P;
     const int g = f % a.G, Pg = a.P / a.G;
     const int ref = iv * a.P + g + a.G * (Pg / 2);
     if (agent == ref) return;
-    const int N = a.N;
-    for (int k = 0; k < a.K; ++k) {
+    const int N = a.N, lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k = warp; k < a.K; k += nw) {
         const float* Ja = a.J + ((size_t)agent * a.K + k) * N * 8;
         const float* Jr = a.J + ((size_t)ref * a.K + k) * N * 8;
-        C2 m[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-        for (int p = threadIdx.x; p < N; p += blockDim.x) {
-            C2 ja[4], jr[4];
-            for (int i = 0; i < 4; ++i) {
-                ja[i] = {Ja[p * 8 + 2 * i], Ja[p * 8 + 2 * i + 1]};
-                jr[i] = {Jr[p * 8 + 2 * i], Jr[p * 8 + 2 * i + 1]};
+        float m[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};  // M[i][j] at 2 (2 i + j) (re, im)
+        for (int p = lane; p < N; p += 32) {
+            F2 ja[4], jr[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                ja[e] = {Ja[p * 8 + 2 * e], Ja[p * 8 + 2 * e + 1]};
+                jr[e] = {Jr[p * 8 + 2 * e], Jr[p * 8 + 2 * e + 1]};
             }
             // M[i][j] += sum_m conj(Ja[m][i]) Jr[m][j]
+#pragma unroll
             for (int i = 0; i < 2; ++i)
-                for (int j = 0; j < 2; ++j)
-                    for (int mm = 0; mm < 2; ++mm) m[i * 2 + j] = cadd(m[i * 2 + j], cm(cconj(ja[mm * 2 + i]), jr[mm * 2 + j]));
+#pragma unroll
+                for (int j = 0; j < 2; ++j) {
+                    const F2 t = fadd(fcm(ja[0 * 2 + i], jr[0 * 2 + j]), fcm(ja[1 * 2 + i], jr[1 * 2 + j]));
+                    m[2 * (2 * i + j)] += t.r;
+                    m[2 * (2 * i + j) + 1] += t.i;
+                }
         }
-        double tot[8];
-        for (int i = 0; i < 4; ++i) {
-            tot[2 * i] = bsum(m[i].r, red);
-            tot[2 * i + 1] = bsum(m[i].i, red);
-        }
-        if (threadIdx.x == 0) {
-            const C2 M00 = {tot[0], tot[1]}, M01 = {tot[2], tot[3]}, M10 = {tot[4], tot[5]}, M11 = {tot[6], tot[7]};
+#pragma unroll
+        for (int e = 0; e < 8; ++e) m[e] = warp_sum_f32(m[e]);
+        float u[8];
+        if (lane == 0) {
+            const C2 M00 = {m[0], m[1]}, M01 = {m[2], m[3]}, M10 = {m[4], m[5]}, M11 = {m[6], m[7]};
             const C2 det = cadd(cm(M00, M11), {-(cm(M01, M10).r), -(cm(M01, M10).i)});
             const double adet = hypot(det.r, det.i);
             const C2 ph = adet > 0 ? C2{det.r / adet, det.i / adet} : C2{1.0, 0.0};
@@ -76,43 +91,64 @@ __global__ void __launch_bounds__(CT) k_gauge(const ConsArgs a) {
             const C2 A00 = cconj(M11), A01 = {-M10.r, M10.i}, A10 = {-M01.r, M01.i}, A11 = cconj(M00);
             const double fro = M00.r * M00.r + M00.i * M00.i + M01.r * M01.r + M01.i * M01.i +
                                M10.r * M10.r + M10.i * M10.i + M11.r * M11.r + M11.i * M11.i;
-            const double s = sqrt(fro + 2.0 * adet);
-            const double is = s > 0 ? 1.0 / s : 0.0;
-            const C2 u00 = cadd(M00, cm(ph, A00)), u01 = cadd(M01, cm(ph, A01));
-            const C2 u10 = cadd(M10, cm(ph, A10)), u11 = cadd(M11, cm(ph, A11));
-            U[0] = {u00.r * is, u00.i * is};
-            U[1] = {u01.r * is, u01.i * is};
-            U[2] = {u10.r * is, u10.i * is};
-            U[3] = {u11.r * is, u11.i * is};
-            if (!(s > 0)) { U[0] = {1, 0}; U[1] = {0, 0}; U[2] = {0, 0}; U[3] = {1, 0}; }
+            const double sq = sqrt(fro + 2.0 * adet);
+            C2 U[4] = {{1, 0}, {0, 0}, {0, 0}, {1, 0}};
+            if (sq > 0) {
+                const double is = 1.0 / sq;
+                const C2 u00 = cadd(M00, cm(ph, A00)), u01 = cadd(M01, cm(ph, A01));
+                const C2 u10 = cadd(M10, cm(ph, A10)), u11 = cadd(M11, cm(ph, A11));
+                U[0] = {u00.r * is, u00.i * is};
+                U[1] = {u01.r * is, u01.i * is};
+                U[2] = {u10.r * is, u10.i * is};
+                U[3] = {u11.r * is, u11.i * is};
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                u[2 * e] = (float)U[e].r;
+                u[2 * e + 1] = (float)U[e].i;
+            }
         }
-        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) u[e] = __shfl_sync(0xffffffffu, u[e], 0);
+        const F2 U[4] = {{u[0], u[1]}, {u[2], u[3]}, {u[4], u[5]}, {u[6], u[7]}};
         float* Jw = a.J + ((size_t)agent * a.K + k) * N * 8;
         float* Gw = a.gradg + ((size_t)agent * a.K + k) * N * 8;
         float* Hw = a.Gm + ((size_t)agent * a.K + k) * N * 4;
-        for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        for (int p = lane; p < N; p += 32) {
+#pragma unroll
             for (int which = 0; which < 2; ++which) {
                 float* X = (which == 0 ? Jw : Gw) + p * 8;
-                C2 x[4], y[4];
-                for (int i = 0; i < 4; ++i) x[i] = {X[2 * i], X[2 * i + 1]};
+                F2 x[4], y[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) x[e] = {X[2 * e], X[2 * e + 1]};
+#pragma unroll
                 for (int r = 0; r < 2; ++r)
-                    for (int n = 0; n < 2; ++n) y[r * 2 + n] = cadd(cm(x[r * 2 + 0], U[0 * 2 + n]), cm(x[r * 2 + 1], U[1 * 2 + n]));
-                for (int i = 0; i < 4; ++i) { X[2 * i] = (float)y[i].r; X[2 * i + 1] = (float)y[i].i; }
+#pragma unroll
+                    for (int n = 0; n < 2; ++n) y[r * 2 + n] = fadd(fm(x[r * 2 + 0], U[0 * 2 + n]), fm(x[r * 2 + 1], U[1 * 2 + n]));
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    X[2 * e] = y[e].r;
+                    X[2 * e + 1] = y[e].i;
+                }
             }
             // G <- U^H G U
             float* Gp = Hw + p * 4;
-            const C2 G00 = {Gp[0], 0}, G11 = {Gp[1], 0}, G01 = {Gp[2], Gp[3]}, G10 = {Gp[2], -Gp[3]};
-            const C2 Gm_[4] = {G00, G01, G10, G11};
-            C2 T[4], R[4];
+            const F2 Gm_[4] = {{Gp[0], 0.f}, {Gp[2], Gp[3]}, {Gp[2], -Gp[3]}, {Gp[1], 0.f}};
+            F2 T[4], R[4];
+#pragma unroll
             for (int r = 0; r < 2; ++r)  // T = G U
-                for (int n = 0; n < 2; ++n) T[r * 2 + n] = cadd(cm(Gm_[r * 2 + 0], U[0 * 2 + n]), cm(Gm_[r * 2 + 1], U[1 * 2 + n]));
+#pragma unroll
+                for (int n = 0; n < 2; ++n) T[r * 2 + n] = fadd(fm(Gm_[r * 2 + 0], U[0 * 2 + n]), fm(Gm_[r * 2 + 1], U[1 * 2 + n]));
+#pragma unroll
             for (int r = 0; r < 2; ++r)  // R = U^H T
-                for (int n = 0; n < 2; ++n) R[r * 2 + n] = cadd(cm(cconj(U[0 * 2 + r]), T[0 * 2 + n]), cm(cconj(U[1 * 2 + r]), T[1 * 2 + n]));
-            Gp[0] = (float)R[0].r; Gp[1] = (float)R[3].r; Gp[2] = (float)R[1].r; Gp[3] = (float)R[1].i;
+#pragma unroll
+                for (int n = 0; n < 2; ++n) R[r * 2 + n] = fadd(fcm(U[0 * 2 + r], T[0 * 2 + n]), fcm(U[1 * 2 + r], T[1 * 2 + n]));
+            Gp[0] = R[0].r;
+            Gp[1] = R[3].r;
+            Gp[2] = R[1].r;
+            Gp[3] = R[1].i;
         }
-        __syncthreads();
     }
-    (void)f;
 }
 
 // One C-ADMM fusion-centre and dual step for one (consensus problem, direction) and ZJ consecutive

@@ -258,28 +258,26 @@ __global__ void __launch_bounds__(256) k_predict(const PredictArgs a, int s_chun
 // Jacobi weights of one agent: gw[k][o][p] = gw[k][p][o] = s_bk = sum_t |c_btk|^2 for the baseline
 // b = (p, o), zero for flagged baselines and o = p (fixed for the whole calibration). Each entry is
 // written by the one slot that holds its station pair: no atomics.
+// One CTA per (diagonal, agent); the entries no slot writes (the diagonal p = o, flagged pairs,
+// the row padding) are zeroed by the launcher first.
 __global__ void k_gram_weights(const float2* C, const DiagDesc* desc, const int* slot, const int* T, float* gw,
                                int D, int K, int N) {
-    const int agent = blockIdx.x;
+    const int d = blockIdx.x, agent = blockIdx.y;
     const int NW = (N + 3) / 4 * 4;  // row stride: 16-byte rows
     float* W = gw + (size_t)agent * K * N * NW;
-    for (int i = threadIdx.x; i < K * N * NW; i += blockDim.x) W[i] = 0.f;
-    __syncthreads();
     const int Ta = T[agent];
-    for (int d = 0; d < D; ++d) {
-        const DiagDesc dsc = desc[(size_t)agent * D + d];
-        for (int it = threadIdx.x; it < dsc.n * K; it += blockDim.x) {
-            const int g = it / K, k = it - g * K;
-            float s = 0.f;
-            for (int t = 0; t < Ta; ++t) {
-                const float2 c = C[dsc.coff + ((size_t)t * dsc.n_pad + g) * K + k];
-                s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
-            }
-            const int sl = slot[dsc.slot_off + g];
-            const int f = sl & 0xff, sc = (sl >> 8) & 0xff;
-            W[((size_t)k * N + f) * NW + sc] = s;
-            W[((size_t)k * N + sc) * NW + f] = s;
+    const DiagDesc dsc = desc[(size_t)agent * D + d];
+    for (int it = threadIdx.x; it < dsc.n * K; it += blockDim.x) {
+        const int g = it / K, k = it - g * K;
+        float s = 0.f;
+        for (int t = 0; t < Ta; ++t) {
+            const float2 c = __ldg(C + dsc.coff + ((size_t)t * dsc.n_pad + g) * K + k);
+            s = fmaf(c.x, c.x, fmaf(c.y, c.y, s));
         }
+        const int sl = slot[dsc.slot_off + g];
+        const int f = sl & 0xff, sc = (sl >> 8) & 0xff;
+        W[((size_t)k * N + f) * NW + sc] = s;
+        W[((size_t)k * N + sc) * NW + f] = s;
     }
 }
 
@@ -427,7 +425,9 @@ cudaError_t launch_predict(const PredictArgs& a, cudaStream_t s) {
 }
 cudaError_t launch_gram_weights(const float2* C, const DiagDesc* desc, const int* slot, const int* T, float* gw,
                                 int A, int D, int K, int N, cudaStream_t s) {
-    k_gram_weights<<<A, 256, 0, s>>>(C, desc, slot, T, gw, D, K, N);
+    const cudaError_t e = cudaMemsetAsync(gw, 0, (size_t)A * K * N * ((N + 3) / 4 * 4) * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    k_gram_weights<<<dim3(D, A), 128, 0, s>>>(C, desc, slot, T, gw, D, K, N);
     return cudaGetLastError();
 }
 // Shared memory of a CTA of the staged statistics pass: the largest V + C block.
