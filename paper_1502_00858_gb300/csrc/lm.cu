@@ -29,9 +29,12 @@ namespace calib {
 namespace {
 
 // At most 512 threads a CTA. With one block per thread (K*N <= 512) at most 64 registers a thread,
-// so that 3 agents' CTAs share an SM (320 agents of 320 threads fit 152 SMs in one wave); larger
-// K*N keeps its blocks in registers instead.
+// so that 3 agents' CTAs share an SM (320 agents of 320 threads fit 152 SMs in one wave); with two
+// (K*N <= 768) at most 384 threads and 80 registers, so that two CTAs share an SM (a few spilled
+// bytes cost less than half the resident agents would); larger K*N keeps its blocks in registers.
 constexpr int LM_MAX_THREADS = 512;
+// Two blocks a thread: at most 384 threads, so that two CTAs share an SM (80 registers a thread).
+constexpr int LM_MAX_THREADS_BPT2 = 384;
 
 struct Blk { float v[8]; };
 
@@ -328,7 +331,7 @@ __device__ void gram_blocks(const LMArgs& a, int agent, const Blk (&j)[BPT], flo
 // PCG initialisation for the next LM step: grad = gradg + Y/2 + rho/2 (J - BZ), r = -grad,
 // p = z = M^-1 r, x = 0, rz = h(r, z).
 template <int BPT>
-__global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_lm_eval(const LMArgs a, const int mode) {
+__global__ void __launch_bounds__(BPT == 2 ? LM_MAX_THREADS_BPT2 : LM_MAX_THREADS, BPT <= 2 ? 2 : 1) k_lm_eval(const LMArgs a, const int mode) {
     extern __shared__ __align__(16) float sm[];  // KN*GT floats (gauge terms), reused for J^H J
     __shared__ float red[4][64];
     __shared__ float Asol[MAX_K * 4];
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_lm_eval(co
 // One PCG step of one agent after the Hessian sweep of its direction p; with last set, also the
 // LM trial point Jt = J + x and the predicted decrease pred = 1/2 h(x, b + r) + mu/2 h(x, x).
 template <int BPT>
-__global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_cg_step(const LMArgs a, const int last) {
+__global__ void __launch_bounds__(BPT == 2 ? LM_MAX_THREADS_BPT2 : LM_MAX_THREADS, BPT <= 2 ? 2 : 1) k_cg_step(const LMArgs a, const int last) {
     __shared__ float red[3][64];
     const int agent = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
     const int N = a.N, KN = a.K * N;
@@ -623,7 +626,7 @@ constexpr double RTR_ACCEPT = 0.1;  // a step is accepted when its ratio exceeds
 // One truncated-CG step of one agent after the Hessian sweep of its direction d (in a.p); with
 // last set, also J' = J + eta and the predicted decrease 1/2 h(eta, b + r).
 template <int BPT>
-__global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_tcg_step(const LMArgs a, const int last) {
+__global__ void __launch_bounds__(BPT == 2 ? LM_MAX_THREADS_BPT2 : LM_MAX_THREADS, BPT <= 2 ? 2 : 1) k_tcg_step(const LMArgs a, const int last) {
     // one area per reduction call site (block_sum<NV> uses NV * 32 floats)
     __shared__ float red_d[3 * 32], red_r[32], red_p[32];
     const int agent = blockIdx.x, T = blockDim.x, tid = threadIdx.x;
@@ -741,7 +744,7 @@ __global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_tcg_step(c
 // the start of the next truncated CG: grad = gradg + Y/2 + rho/2 (J - BZ), r = d = -grad, eta = 0.
 // The begin modes set Delta_bar = ||J||_h and Delta = Delta_bar / 8.
 template <int BPT>
-__global__ void __launch_bounds__(LM_MAX_THREADS, BPT == 1 ? 2 : 1) k_rtr_eval(const LMArgs a, const int mode) {
+__global__ void __launch_bounds__(BPT == 2 ? LM_MAX_THREADS_BPT2 : LM_MAX_THREADS, BPT <= 2 ? 2 : 1) k_rtr_eval(const LMArgs a, const int mode) {
     extern __shared__ __align__(16) float sm[];  // KN*GT floats (gauge terms)
     __shared__ float red[4][64];
     __shared__ float Asol[MAX_K * 4];
@@ -931,7 +934,7 @@ __global__ void __launch_bounds__(256) k_hv_output(const LMArgs a, float* out) {
 struct LMShape { int bpt, threads; };
 LMShape lm_shape(int KN) {
     int bpt = 1;
-    while ((KN + bpt - 1) / bpt > LM_MAX_THREADS) bpt *= 2;
+    while ((KN + bpt - 1) / bpt > (bpt == 2 ? LM_MAX_THREADS_BPT2 : LM_MAX_THREADS)) bpt *= 2;
     const int t = (KN + bpt - 1) / bpt;
     return LMShape{bpt, ((t + 31) / 32) * 32};
 }
