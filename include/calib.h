@@ -255,8 +255,9 @@ int calib_autotune(calib_ctx* ctx, int* split, int* split_trial, int cap, int* c
  * (copies of float32 master weights), float32 accumulation; AdamW on the mean squared error.
  * Weights are a flat float32 array [W_1 (width x 17), b_1, ..., W_last (8 x width), b_last],
  * row-major; calib_mlp_num_params gives its length. A network has its own stream (cuda_stream
- * NULL = its own) and is not thread-safe. The paper has no network: this is the warm-start
- * pattern of the build, judged by the ADMM's own objective (calib_warm_start). */
+ * NULL = its own) and is not thread-safe. The paper has no network: it refines the paper's
+ * previous-solution start, and its output is kept only where the ADMM's own objective
+ * accepts it (calib_warm_start). */
 typedef struct calib_mlp calib_mlp;
 int calib_mlp_create(calib_mlp** out, int n_in, int width, int depth, int n_out, void* cuda_stream);
 long long calib_mlp_num_params(calib_mlp* mlp);
